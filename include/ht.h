@@ -1,0 +1,131 @@
+/*
+ * ht.h -- C ABI of libht, a GB300 (sm_103a) implementation of the
+ * Householder-based Hessenberg-triangular (HT) reduction of Bujanovic,
+ * Karlsson and Kressner, "A Householder-based algorithm for
+ * Hessenberg-triangular reduction" (arXiv 1710.08538).
+ *
+ * Problem (Sec. 1 and Sec. 3, Algorithm 1): given A (n x n) and B (n x n,
+ * upper triangular), compute orthogonal Q and Z such that H = Q^T A Z is upper
+ * Hessenberg and T = Q^T B Z is upper triangular; Q and Z start as the
+ * identity.  A is overwritten by H and B by T, as LAPACK's DGGHRD does.
+ *
+ * Conventions for every call below
+ *   - All matrices are FP64, column-major, in device memory owned by the
+ *     caller (unless a pointer is documented as a host pointer).
+ *   - Leading dimensions must be >= max(1, n).
+ *   - Only the upper triangle of B is read; its strictly lower part is
+ *     written with exact zeros on return.  Entries of H below the first
+ *     subdiagonal are exact zeros on return.
+ *   - Work is queued on `stream` (a cudaStream_t; NULL is the legacy default
+ *     stream).  The calls synchronize `stream` once per panel to read the
+ *     number of reflectors the panel produced, so they return after the
+ *     reduction has finished.
+ *   - Return value: HT_OK, a negative value -i when argument i is invalid
+ *     (LAPACK INFO style), or one of the positive error codes below.  A failure
+ *     of iterative refinement inside the method is not an error: it triggers
+ *     the early absorption of Sec. 3.2.2c.
+ *   - Thread safety: calls on different streams may run concurrently from
+ *     different host threads; each call uses its own workspace.
+ */
+#ifndef HT_H
+#define HT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* ht_stream_t; /* same type as cudaStream_t */
+
+enum {
+  HT_OK = 0,
+  HT_ERR_CUDA = 1001,            /* a CUDA runtime call failed */
+  HT_ERR_NOMEM = 1002,           /* device workspace could not be allocated */
+  HT_ERR_TIMEOUT = 1003,         /* a bounded device-side wait gave up */
+  HT_ERR_NONFINITE = 1004,       /* A or B holds a NaN or an infinity */
+  HT_ERR_NOT_IMPLEMENTED = 1005, /* option combination not available */
+  HT_ERR_INTERNAL = 1006         /* a device-side consistency check failed */
+};
+
+/* Precision of the bulk (level-3) updates of the absorption, Sec. 3.3. */
+enum {
+  HT_PREC_FP64 = 0, /* native FP64 (DFMA) */
+  HT_PREC_EMU = 1   /* FP64 emulated by split BF16 products on tensor cores */
+};
+
+/* Tuning and test options of ht_reduce_ex.  Zero-initialise, then set
+ * fields; a zero field takes its default. */
+typedef struct ht_options {
+  int nb;              /* panel width (Sec. 3.2); default 32 */
+  int max_ir;          /* iterative-refinement steps per column (Sec. 2.3); default 10, < 0 means 0 */
+  double ir_tol_scale; /* multiplies the IR tolerance 2u||B||_F; default 1.0, < 0 means 0 */
+  int precision;       /* HT_PREC_*; default HT_PREC_FP64 */
+  int emu_slices;      /* BF16 slices per operand for HT_PREC_EMU; 0 = automatic */
+  uint64_t seed;       /* key of the singular-B perturbation (Remark 2.2) */
+  int reserved[8];
+} ht_options;
+
+/* Per-call counters, the columns of the paper's Tables 3 and 4 plus time. */
+typedef struct ht_stats {
+  int panels;              /* panel reductions started */
+  int early_absorptions;   /* panels ended by an IR failure (Sec. 3.2.2c) */
+  long long ir_steps;      /* correction solves of iterative refinement */
+  long long cols_with_ir;  /* columns that needed at least one correction */
+  int perturbed_pivots;    /* zero diagonal entries of B replaced (Remark 2.2) */
+  double ms_panel;         /* device time of the panel reductions (Sec. 3.2) */
+  double ms_absorb;        /* device time of the absorptions (Sec. 3.3) */
+  double flops_nominal;    /* leading-order flop count of the blocked method */
+} ht_stats;
+
+/*
+ * ht_reduce -- HT reduction of one pencil (Algorithm 1, HouseHT).
+ *   n        order of the pencil, n >= 0
+ *   A, lda   device, n x n; overwritten by H = Q^T A Z
+ *   B, ldb   device, n x n upper triangular; overwritten by T = Q^T B Z
+ *   Q, Z     device, n x n with leading dimension n; written with the
+ *            accumulated transforms when want_qz != 0 (may be NULL otherwise)
+ *   want_qz  0: do not form Q and Z
+ *   stream   CUDA stream
+ * n <= 2 leaves A and B unchanged and sets Q = Z = I (the loop of
+ * Algorithm 1 is empty).
+ */
+int ht_reduce(int n, double* A, int lda, double* B, int ldb, double* Q, double* Z, int want_qz,
+              ht_stream_t stream);
+
+/* ht_reduce_ex -- as ht_reduce with leading dimensions for Q and Z, options
+ * (NULL = defaults) and counters (NULL = not wanted). */
+int ht_reduce_ex(int n, double* A, int lda, double* B, int ldb, double* Q, int ldq, double* Z, int ldz,
+                 int want_qz, const ht_options* opt, ht_stats* stats, ht_stream_t stream);
+
+/*
+ * ht_reduce_batched -- HT reduction of `batch` independent pencils of
+ * (possibly different) orders.
+ *   n, lda, ldb   HOST arrays of length batch
+ *   A, B, Q, Z    HOST arrays of `batch` device pointers (Q[i], Z[i] have
+ *                 leading dimension n[i]; ignored when want_qz == 0)
+ * Each pencil follows the rules of ht_reduce.  Pencils are independent; the
+ * library orders them largest first.
+ */
+int ht_reduce_batched(int batch, const int* n, double* const* A, const int* lda, double* const* B,
+                      const int* ldb, double* const* Q, double* const* Z, int want_qz, ht_stream_t stream);
+
+/* ht_last_device_status -- status word written by the device during the
+ * last call on `stream` from this host thread (HT_OK, HT_ERR_TIMEOUT,
+ * HT_ERR_NONFINITE, HT_ERR_INTERNAL). */
+int ht_last_device_status(ht_stream_t stream, int* status);
+
+/* ht_finalize -- release every cached workspace of this process. */
+int ht_finalize(void);
+
+/* ht_status_string -- static description of a return code. */
+const char* ht_status_string(int status);
+
+/* ht_version -- library version string. */
+const char* ht_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HT_H */

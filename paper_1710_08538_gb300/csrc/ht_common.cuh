@@ -1,0 +1,214 @@
+// Internal declarations shared by the CUDA translation units of libht.
+//
+// Index conventions (0-based; the paper is 1-based):
+//   s      first unreduced column of A at the start of a panel (Sec. 3.2)
+//   k      reflectors accumulated in the panel, j = s + k
+//   m      n - s - 1, rows of the trailing system B(s+1:n, s+1:n)
+//   p      n - j - 1, rows of V2 and U2 (Sec. 3.3.1a, 3.3.2a)
+// Panel factors are stored with "local" rows r = global row - (s + 1):
+//   U(r, i), V(r, i)  ld = n, r in [0, m)   (U1 = rows 0..k-1, U2 = rows k..m-1)
+//   Y(row, i)         ld = n, global rows   (rows 0..s formed after the panel)
+//   S, T              ld = nbmax, upper triangular
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ht.h"
+
+#define HT_THREADS 256
+#define HT_TRSV_BS 64          // row block of the triangular solve / multiply
+#define HT_NB_MAX 64           // largest panel width (windows live in shared memory)
+#define HT_BIG_EXP 500         // rescale threshold 2^500 of the scaled solve
+#define HT_SPIN_LIMIT (1 << 22)  // ~ a few seconds of polling, then HT_ERR_TIMEOUT
+
+// ---------------------------------------------------------------------------
+// Window / block layout of the absorption chains (Sec. 3.3, Remark 3.2).
+// p rows of V2 (or U2), k reflectors.  The first window has kt rows with
+// k < kt <= 2k (or p rows when p <= 2k); the others have 2k rows, overlap k.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int ht_first_window(int p, int k) {
+  if (p <= 2 * k) return p;
+  int q = (p - 2 * k + k - 1) / k;
+  return p - k * q;
+}
+__host__ __device__ inline int ht_num_windows(int p, int k) {
+  int kt = ht_first_window(p, k);
+  return (kt >= p) ? 1 : 1 + (p - kt) / k;
+}
+// QL chain on V2, top to bottom: window i covers rows [r0, r1).
+__host__ __device__ inline void ht_ql_window(int p, int k, int i, int* r0, int* r1) {
+  int kt = ht_first_window(p, k);
+  if (i == 0) { *r0 = 0; *r1 = kt; return; }
+  *r0 = kt - k + (i - 1) * k;
+  *r1 = *r0 + 2 * k;
+}
+// QR chain on U2, bottom to top: window i covers rows [r0, r1).
+__host__ __device__ inline void ht_qr_window(int p, int k, int i, int* r0, int* r1) {
+  int kt = ht_first_window(p, k);
+  if (i == 0) { *r0 = p - kt; *r1 = p; return; }
+  *r1 = p - kt + k - (i - 1) * k;
+  *r0 = *r1 - 2 * k;
+}
+// Column blocks of B(:, j+1:n) after the QL chain (small block first).
+__host__ __device__ inline int ht_num_right_blocks(int p, int k) {
+  if (p <= k) return 1;
+  int b0 = ht_first_window(p, k) - k;
+  return 1 + (p - b0) / k;
+}
+__host__ __device__ inline void ht_right_block(int p, int k, int b, int* c0, int* c1) {
+  if (p <= k) { *c0 = 0; *c1 = p; return; }
+  int b0 = ht_first_window(p, k) - k;
+  if (b == 0) { *c0 = 0; *c1 = b0; return; }
+  *c0 = b0 + (b - 1) * k;
+  *c1 = *c0 + k;
+}
+// Row blocks of B(j+1:n, :) after the QR chain (small block last).
+__host__ __device__ inline int ht_num_left_blocks(int p, int k) {
+  if (p <= k) return 1;
+  int bl = ht_first_window(p, k) - k;
+  return (p - bl) / k + 1;
+}
+__host__ __device__ inline void ht_left_block(int p, int k, int b, int* r0, int* r1) {
+  if (p <= k) { *r0 = 0; *r1 = p; return; }
+  int bl = ht_first_window(p, k) - k;
+  int nfull = (p - bl) / k;
+  if (b < nfull) { *r0 = b * k; *r1 = *r0 + k; return; }
+  *r0 = nfull * k; *r1 = p;
+}
+
+// ---------------------------------------------------------------------------
+// A chain of orthogonal transforms G_i = I - Vw_i Ww_i^T (regular WY form,
+// Sec. 2.4), each acting on `width` consecutive rows/columns starting at
+// `offset`.  Vw_i and Ww_i are width x nrefl, column-major, ld = width, at
+// wy + i * stride (Vw) and wy + i * stride + HT_WY_HALF(stride) (Ww).
+// ---------------------------------------------------------------------------
+struct WyWin {
+  int offset;  // first row/column acted on, relative to the chain origin
+  int width;   // rows/columns acted on
+  int nrefl;   // reflectors (columns of Vw, Ww)
+  int limit;   // structural bound used by the sweeps (see ht_apply.cu)
+};
+
+struct PanelStatus {
+  int k_done;        // reflector pairs accumulated by the panel
+  int failed;        // 1 when the panel stopped on an IR failure
+  int ir_steps;      // correction solves in this panel
+  int cols_with_ir;  // columns with >= 1 correction
+  int error;         // HT_OK or an HT_ERR_* code raised on the device
+  int perturbed;     // zero pivots replaced before the panel
+  int pad[2];
+};
+
+// Device workspace of one reduction (sizes for order n and panel width nb).
+struct HtWork {
+  int n, nb, G;            // order, panel width, CTAs of the cooperative panel
+  double *U, *V, *Y;       // n x nb each (ld n)
+  double *S, *T;           // nb x nb each (ld nb)
+  double *vec;             // 8 vectors of length n (see ht_panel.cu)
+  double *part;            // G x HT_PART_STRIDE partial sums
+  double *ypart;           // ychunks x n partial GEMV sums
+  int ychunks;
+  double *invd;            // reciprocal of diag(B), length n
+  int *flags, *exps;       // TRSV block flags / scale exponents (n / 64 + 1 each)
+  unsigned *epoch;         // TRSV epoch counter (device)
+  PanelStatus *status;     // device status of the last panel
+  double *bnorm;           // ||B||_F (device scalar)
+  double *wyR, *wyL;       // WY stores of the QL (V2) and QR (U2) chains
+  double *wyRR, *wyLR;     // WY stores of the RQ and QR restore chains
+  size_t wy_cap;           // doubles per store (>= (p/k + 2) * 4k^2 for every k <= nb)
+  double *L1, *R1;         // L-hat_1 and R-tilde_1 (nb x nb)
+  double *V2w, *U2w;       // working copies of V2, U2 (n x nb)
+  double *tmp1, *tmp2, *tmp3;  // n x nb scratch
+  double *small;           // nb x nb scratch (4 of them)
+  int *err;                // device error word
+  unsigned epoch_host;     // next TRSV epoch (host shadow)
+  cudaStream_t stream;
+};
+#define HT_PART_STRIDE 80   // >= nb + 8 for nb <= 64 ... plus norms
+#define HT_NVEC 8
+
+// ---------------------------------------------------------------------------
+// Launchers (each returns a cudaError_t of the launch)
+// ---------------------------------------------------------------------------
+cudaError_t ht_launch_prepare_B(HtWork& w, double* B, int ldb, int s, uint64_t seed, int first);
+cudaError_t ht_launch_panel(HtWork& w, double* A, int lda, const double* B, int ldb, int s, int kmax,
+                            double tol_scale, int max_ir);
+cudaError_t ht_gemm(cudaStream_t st, char ta, char tb, int M, int N, int K, double alpha, const double* A, int lda,
+                    const double* Bm, int ldb, double beta, double* C, int ldc);
+cudaError_t ht_launch_factor_chain(cudaStream_t st, int mode, double* X, int ldx, int p, int k, double* wy,
+                                   size_t stride, double* out_tri);
+cudaError_t ht_launch_factor_block(cudaStream_t st, int mode, double* X, int ldx, int rows, int cols, double* wy,
+                                   size_t stride);
+cudaError_t ht_sweep(cudaStream_t st, int right, double* X, long ldx, int line0, int nlines, int origin,
+                     const double* wy, long stride, int mode, int p, int k, int t0, int t1, int use_limit,
+                     int limit_base);
+cudaError_t ht_apply_single(cudaStream_t st, int right, double* X, long ldx, int line0, int nlines, int origin,
+                            int width, int nrefl, const double* wy, long stride);
+cudaError_t ht_rankk_right_w(cudaStream_t st, double* X, long ldx, int nrows, int c1, int w1, int k,
+                             const double* V1, int ldv1, const double* T, int ldt);
+cudaError_t ht_rankk_left(cudaStream_t st, double* X, long ldx, int col0, int ncols, int r0, int w1, int k,
+                          const double* Ut, int ldu, const double* S, int lds);
+int ht_panel_max_ctas(int nb);
+cudaError_t ht_launch_rankk_right(cudaStream_t st, double* X, long ldx, int nrows, int c1, int c2, int k,
+                                  const double* V1, int ldv1, const double* L1, int ldl1, const double* T, int ldt);
+cudaError_t ht_launch_rankk_left(cudaStream_t st, double* X, long ldx, int ncols, int r0, int k, const double* Ut,
+                                 int ldu, const double* S, int lds);
+cudaError_t ht_launch_zero(cudaStream_t st, double* X, long ldx, int rows, int cols, int lower_only);
+cudaError_t ht_launch_set_identity(cudaStream_t st, double* X, long ldx, int n);
+cudaError_t ht_launch_check_finite(cudaStream_t st, const double* X, long ldx, int n, int upper_only, int* err);
+
+// WY store helpers
+__host__ __device__ inline size_t ht_wy_half(size_t stride) { return stride / 2; }
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+__device__ __forceinline__ double ht_warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double ht_warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+// Block-wide sum; `red` is shared scratch of >= 32 doubles.  All threads get the result.
+__device__ __forceinline__ double ht_block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = ht_warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+  if (wid == 0) t = ht_warp_sum(t);
+  if (threadIdx.x == 0) red[0] = t;
+  __syncthreads();
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+__device__ __forceinline__ double ht_block_max(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = ht_warp_max(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+  if (wid == 0) t = ht_warp_max(t);
+  if (threadIdx.x == 0) red[0] = t;
+  __syncthreads();
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+__device__ __forceinline__ int ht_ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void ht_st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+#endif

@@ -1,0 +1,72 @@
+"""The C ABI without a GPU: every function declared in include/ht.h is
+exported by libht.so, and host-side argument errors come back synchronously
+as LAPACK-style negative codes before any CUDA call."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def htlib():
+    import __graft_entry__ as g
+    from paper_1710_08538_gb300 import _build
+    _build.build()
+    import paper_1710_08538_gb300 as ht
+    return ht
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "ht.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(ht_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("ht_reduce", "ht_reduce_batched", "ht_reduce_ex", "ht_last_device_status", "ht_finalize"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(htlib):
+    L = htlib.lib()
+    for name in _declared_functions():
+        assert hasattr(L, name), name
+    assert set(htlib.EXPORTED) >= set(_declared_functions())
+
+
+def test_version_and_status_strings(htlib):
+    assert b"sm_103a" in htlib.lib().ht_version()
+    assert htlib.status_string(0) == "success"
+    assert "NaN" in htlib.status_string(htlib.HT_ERR_NONFINITE)
+    assert htlib.status_string(-3) == "invalid argument"
+
+
+@pytest.mark.parametrize("args,code", [
+    ((-1, 8, 8, 1), -1),    # n < 0
+    ((10, 5, 10, 1), -3),   # lda < n
+    ((10, 10, 9, 1), -5),   # ldb < n
+])
+def test_argument_errors(htlib, args, code):
+    n, lda, ldb, want = args
+    fake = 0x1000  # never dereferenced: the arguments are rejected first
+    rc = htlib.lib().ht_reduce(n, fake, lda, fake, ldb, fake, fake, want, None)
+    assert rc == code
+
+
+def test_null_pointers_rejected(htlib):
+    L = htlib.lib()
+    assert L.ht_reduce(4, None, 4, 0x1000, 4, 0x1000, 0x1000, 1, None) == -2
+    assert L.ht_reduce(4, 0x1000, 4, None, 4, 0x1000, 0x1000, 1, None) == -4
+    assert L.ht_reduce(4, 0x1000, 4, 0x1000, 4, None, 0x1000, 1, None) == -6
+    assert L.ht_reduce_batched(-1, None, None, None, None, None, None, None, 0, None) == -1
+
+
+def test_options_rejected_before_device_work(htlib):
+    opts = htlib.options(nb=128)
+    L = htlib.lib()
+    import ctypes
+    rc = L.ht_reduce_ex(4, 0x1000, 4, 0x1000, 4, 0x1000, 4, 0x1000, 4, 1, ctypes.byref(opts), None, None)
+    assert rc == htlib.HT_ERR_NOT_IMPLEMENTED
