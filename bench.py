@@ -1,0 +1,310 @@
+#!/usr/bin/env python3
+"""Benchmark of the Householder-based Hessenberg-triangular reduction (libht).
+
+One step = one HT reduction (Algorithm 1, with Q and Z) of one synthetic
+pencil of order n = 16384 with A ~ N(0,1) and B = triu(N(0,1)) + 4 I, the
+single-pencil workload the headline metric is quoted on.  Inputs are drawn on
+the host with numpy (PCG64, seeded), kept resident in HBM and copied into the
+working buffers at the start of every step (the reduction overwrites them).
+
+Printed: one JSON line with the seconds per pencil, the effective TFLOP/s at
+the fixed flop count F(n) = 116 n^3 / 3 (leading-order flops of the blocked
+method with Q and Z), the backward errors of the last step,
+the roofline of the dominant launch class, clocks sampled during the timed
+region, an end-to-end number through the C ABI with host buffers, and a CPU
+baseline (the unblocked Givens reduction of the CPU oracle on a bounded
+sample, extrapolated by n^3).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--n 16384] [--nb 32]
+  python bench.py --impl reference     # CPU oracle arm, bounded sample
+Multi-GPU (torchrun): independent replicas, one pencil per rank per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "s/pencil & eff. TFLOP/s (n=16384, Q,Z) at bwd err ≤1e-12: emulated vs plain FP64"
+FP64_PEAK_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12  # SMs x SMSPs x DFMA/clk x 2 flop x max clock
+
+
+def f_nom(n: int) -> float:
+    """Leading-order flops of the blocked HouseHT with Q and Z."""
+    return 116.0 * n ** 3 / 3.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--n", type=int, default=16384)
+    p.add_argument("--nb", type=int, default=32)
+    p.add_argument("--seed", type=int, default=3000)
+    p.add_argument("--precision", default="fp64", choices=["fp64", "emu"])
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--cpu-sample", type=int, default=1024)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline key)
+# ----------------------------------------------------------------------------
+def cpu_oracle_time(n_sample: int, seed: int) -> tuple[float, float]:
+    """Seconds of the oracle's unblocked Givens HT reduction (Q and Z) of one
+    pencil of order n_sample, and its extrapolation to n by n^3."""
+    import oracle
+    from paper_1710_08538_gb300 import pencils
+    oracle.build()
+    A, B = pencils.shifted_triu(n_sample, seed)
+    t0 = time.perf_counter()
+    oracle.givens_ht(A, B)
+    return time.perf_counter() - t0, n_sample
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    times = []
+    for _ in range(max(args.warmup, 0)):
+        cpu_oracle_time(min(args.cpu_sample, 512), args.seed)
+    for _ in range(args.steps):
+        dt, ns = cpu_oracle_time(args.cpu_sample, args.seed)
+        times.append(dt * (args.n / ns) ** 3)
+    sec = statistics.mean(times)
+    value = f_nom(args.n) / sec / 1e12
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "higher_is_better": True,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "s_per_pencil": sec,
+        "ms_per_step": sec * 1e3, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"single pencil n={args.n}, A~N(0,1), B=triu(N(0,1))+4I, Q and Z", "n": args.n},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+                         "sample": f"unblocked Givens HT reduction (oracle) of one n={args.cpu_sample} pencil per "
+                                   f"step, extrapolated to n={args.n} by n^3"},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "vs_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__ as g
+    g.build()
+    import paper_1710_08538_gb300 as ht
+    from paper_1710_08538_gb300 import check, pencils
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    n, nb = args.n, args.nb
+    prec = ht.HT_PREC_FP64 if args.precision == "fp64" else ht.HT_PREC_EMU
+
+    # inputs: host (numpy PCG64, seeded per rank) -> pinned -> resident device copies
+    A_np, B_np = pencils.shifted_triu(n, args.seed + rank)
+    A_host = torch.from_numpy(np.asfortranarray(A_np).ravel(order="F")).pin_memory()
+    B_host = torch.from_numpy(np.asfortranarray(B_np).ravel(order="F")).pin_memory()
+    del A_np, B_np
+
+    def colmajor_empty():
+        return torch.empty((n, n), dtype=torch.float64, device=dev).t()
+
+    A0, B0 = colmajor_empty(), colmajor_empty()
+    A0.copy_(A_host.view(n, n).t())
+    B0.copy_(B_host.view(n, n).t())
+    A, B, Q, Z = colmajor_empty(), colmajor_empty(), colmajor_empty(), colmajor_empty()
+    stream = torch.cuda.current_stream(dev)
+
+    def step(stats=False, profile=0):
+        A.copy_(A0)
+        B.copy_(B0)
+        return ht.reduce(A, B, Q, Z, want_qz=True, opts=ht.options(nb=nb, precision=prec, profile=profile),
+                         stream=stream, with_stats=stats)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    agg = None
+    for _ in range(args.steps):
+        st = step(stats=True, profile=1)
+        if agg is None:
+            agg = {k: (list(v) if isinstance(v, list) else v) for k, v in st.items()}
+        else:
+            for k, v in st.items():
+                if isinstance(v, list):
+                    agg[k] = [a + b for a, b in zip(agg[k], v)]
+                elif isinstance(v, (int, float)):
+                    agg[k] += v
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    ms = float(t.item())
+    sec_per_pencil = ms / 1e3 / args.steps  # per rank; ranks run concurrently
+    value = world * args.steps * f_nom(n) / (ms / 1e3) / 1e12
+
+    # backward error of the last step (probes: exact FP64 GEMMs would take minutes)
+    rep = check.invariants(A0, B0, A, B, Q, Z, probes=16, seed=7)
+
+    # roofline of the dominant launch class (device time by CUDA events in the library)
+    cls_ms = agg["ms_by_class"]
+    cls_fl = agg["flops_by_class"]
+    cls_n = agg["launches_by_class"]
+    dom = max(range(7), key=lambda i: cls_ms[i])
+    launches = sum(cls_n[:7])
+    ach = cls_fl[dom] / (cls_ms[dom] / 1e3) / 1e12 if cls_ms[dom] > 0 else 0.0
+    roof = {"kernel_class": ht.CLASS_NAMES[dom], "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+            "launches": int(cls_n[dom]), "avg_launch_ms": cls_ms[dom] / max(cls_n[dom], 1),
+            "peak_source": "FP64 DFMA units x max clock (152 SMs x 4 x 0.5 DFMA/clk x 2 x 2.07 GHz); "
+                           "measured DFMA loop 1.19 TFLOP/s"}
+
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        # end to end through the C ABI with host buffers: H2D of A, B, the
+        # reduction, D2H of H, T, Q, Z, all inside the timed interval
+        H_host = torch.empty(n * n, dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        A.copy_(A_host.view(n, n).t(), non_blocking=True)
+        B.copy_(B_host.view(n, n).t(), non_blocking=True)
+        rc = ht.reduce_plain(n, A.data_ptr(), n, B.data_ptr(), n, Q.data_ptr(), Z.data_ptr(), 1, stream.cuda_stream)
+        if rc != 0:
+            raise RuntimeError(f"ht_reduce failed: {rc}")
+        for X in (A, B, Q, Z):
+            H_host.view(n, n).t().copy_(X, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        e2e = {"value": f_nom(n) / dt / 1e12, "unit": "TFLOP/s", "s_per_pencil": dt,
+               "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": 4 * n * n * 8}
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        dt, ns = cpu_oracle_time(args.cpu_sample, args.seed)
+        est = dt * (n / ns) ** 3
+        cpu = {"value": f_nom(n) / est / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+               "s_per_pencil_extrapolated": est,
+               "sample": f"unblocked Givens HT reduction (oracle, C, 1 thread) of one n={ns} pencil of the same "
+                         f"workload in {dt:.2f} s, extrapolated to n={n} by n^3"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "higher_is_better": True,
+            "s_per_pencil": sec_per_pencil, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "precision_path": args.precision,
+            "config": {"workload": f"single pencil n={n}, A~N(0,1), B=triu(N(0,1))+4I, Q and Z accumulated",
+                       "n": n, "nb": nb, "flop_count": "116 n^3 / 3",
+                       "l2": "inputs (2 x 2 GiB) exceed the 129 MB L2; no flush",
+                       "parallelism": f"replicas x{world}"},
+            "bwd_err": {"a": rep["bwd_a"], "b": rep["bwd_b"], "orth_q": rep["orth_q"], "orth_z": rep["orth_z"],
+                        "structure_ok": rep["h_nonzeros_below_subdiag"] == 0 and rep["t_nonzeros_below_diag"] == 0,
+                        "probes": 16},
+            "stats": {"panels": agg["panels"], "early_absorptions": agg["early_absorptions"],
+                      "ir_steps": agg["ir_steps"], "cols_with_ir": agg["cols_with_ir"],
+                      "ms_by_class": dict(zip(ht.CLASS_NAMES[:7], cls_ms[:7]))},
+            "roofline": roof,
+            "clocks": clk,
+            "gpu_launches": int(launches),
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -64,8 +64,21 @@ typedef struct ht_options {
   int precision;       /* HT_PREC_*; default HT_PREC_FP64 */
   int emu_slices;      /* BF16 slices per operand for HT_PREC_EMU; 0 = automatic */
   uint64_t seed;       /* key of the singular-B perturbation (Remark 2.2) */
-  int reserved[8];
+  int profile;         /* 1: time every launch by class into ht_stats (adds syncs) */
+  int reserved[7];
 } ht_options;
+
+/* Launch classes of ht_stats.ms_by_class / flops_by_class / launches_by_class. */
+enum {
+  HT_CLASS_PANEL = 0,        /* cooperative panel reduction (Sec. 3.2) */
+  HT_CLASS_CHAIN_FACTOR = 1, /* QL / QR chains of V2 and U2 (Sec. 3.3.1b, 3.3.2b) */
+  HT_CLASS_RESTORE = 2,      /* RQ / QR restore steps on B (Sec. 3.3.1e, 3.3.2f) */
+  HT_CLASS_SWEEP = 3,        /* chain applications to A, B, Q, Z */
+  HT_CLASS_RANKK = 4,        /* rank-k corrections with V1, L1, U1, R1 */
+  HT_CLASS_GEMM = 5,         /* deferred Y rows (Remark 3.1), spike update */
+  HT_CLASS_OTHER = 6,        /* preparation of B, zeroing, copies */
+  HT_NCLASS = 8
+};
 
 /* Per-call counters, the columns of the paper's Tables 3 and 4 plus time. */
 typedef struct ht_stats {
@@ -76,7 +89,11 @@ typedef struct ht_stats {
   int perturbed_pivots;    /* zero diagonal entries of B replaced (Remark 2.2) */
   double ms_panel;         /* device time of the panel reductions (Sec. 3.2) */
   double ms_absorb;        /* device time of the absorptions (Sec. 3.3) */
-  double flops_nominal;    /* leading-order flop count of the blocked method */
+  double flops_nominal;    /* flops of the operations launched (counted per launch) */
+  double ms_by_class[HT_NCLASS];        /* device time per launch class (profile = 1) */
+  double flops_by_class[HT_NCLASS];     /* algorithmic flops per launch class */
+  long long launches_by_class[HT_NCLASS];
+  double panel_phase_ms[24];            /* panel (0-15) and restore (16-19) time by phase (profile = 1) */
 } ht_stats;
 
 /*

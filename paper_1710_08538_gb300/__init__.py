@@ -36,16 +36,25 @@ EXPORTED = ["ht_reduce", "ht_reduce_ex", "ht_reduce_batched", "ht_last_device_st
 class HtOptions(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int), ("max_ir", ctypes.c_int), ("ir_tol_scale", ctypes.c_double),
                 ("precision", ctypes.c_int), ("emu_slices", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("reserved", ctypes.c_int * 8)]
+                ("profile", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
 
 
 class HtStats(ctypes.Structure):
     _fields_ = [("panels", ctypes.c_int), ("early_absorptions", ctypes.c_int), ("ir_steps", ctypes.c_longlong),
                 ("cols_with_ir", ctypes.c_longlong), ("perturbed_pivots", ctypes.c_int),
-                ("ms_panel", ctypes.c_double), ("ms_absorb", ctypes.c_double), ("flops_nominal", ctypes.c_double)]
+                ("ms_panel", ctypes.c_double), ("ms_absorb", ctypes.c_double), ("flops_nominal", ctypes.c_double),
+                ("ms_by_class", ctypes.c_double * 8), ("flops_by_class", ctypes.c_double * 8),
+                ("launches_by_class", ctypes.c_longlong * 8), ("panel_phase_ms", ctypes.c_double * 24)]
 
     def as_dict(self) -> dict:
-        return {name: getattr(self, name) for name, _ in self._fields_}
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if hasattr(v, "__len__") else v
+        return out
+
+
+CLASS_NAMES = ["panel", "chain_factor", "restore", "sweep", "rankk", "gemm", "other", "unused"]
 
 
 class HtError(RuntimeError):
@@ -123,10 +132,11 @@ def _stream_ptr(stream) -> int:
 
 
 def options(nb: int = 0, max_ir: int = 0, ir_tol_scale: float = 0.0, precision: int = HT_PREC_FP64,
-            emu_slices: int = 0, seed: int = 0) -> HtOptions:
+            emu_slices: int = 0, seed: int = 0, profile: int = 0) -> HtOptions:
     o = HtOptions()
     o.nb, o.max_ir, o.ir_tol_scale, o.precision, o.emu_slices, o.seed = nb, max_ir, ir_tol_scale, precision, \
         emu_slices, seed
+    o.profile = profile
     return o
 
 

@@ -37,6 +37,7 @@ struct PoolEntry {
   HtWork w;
   void* base;
   PanelStatus* host_status;  // pinned
+  unsigned long long* pt_dev; // panel phase timers
 };
 std::mutex g_pool_mu;
 std::vector<PoolEntry*> g_pool;
@@ -66,10 +67,18 @@ int alloc_work(PoolEntry* e, int n, int nb) {
   const size_t oWy = take(4 * w.wy_cap);
   const size_t oL1 = take((size_t)HT_NB_MAX * HT_NB_MAX), oR1 = take((size_t)HT_NB_MAX * HT_NB_MAX);
   const size_t oT1 = take(nn * 2 * nb), oT2 = take(nn * 2 * nb), oT3 = take(nn * 2 * nb);
+  const size_t oU2w = take(nn * nb);
   const size_t oSmall = take((size_t)4 * 2 * HT_NB_MAX * HT_NB_MAX);
   const size_t oFlags = take((size_t)nblk);  // ints, over-allocated as doubles
   const size_t oExps = take((size_t)nblk);
   const size_t oMisc = take(16);
+  const size_t oPt = take(32);
+  const int nbi = (n + HT_TRSV_BI - 1) / HT_TRSV_BI + 1;
+  const size_t oXinv = take((size_t)nbi * HT_TRSV_BI * HT_TRSV_BI);
+  const size_t oSafe = take((size_t)nbi);
+  const size_t oXmax = take(256);
+  const size_t oTst = take(nn * nb + 4 * (size_t)nb * nb);  // (p/k + 1) T factors of k^2 each
+  const size_t oWpart = take((size_t)((n + 4 * HT_TRSV_BS - 1) / (4 * HT_TRSV_BS) + 1) * nn);
   void* base = nullptr;
   if (cudaMalloc(&base, total) != cudaSuccess) return HT_ERR_NOMEM;
   cudaMemset(base, 0, total);
@@ -87,6 +96,7 @@ int alloc_work(PoolEntry* e, int n, int nb) {
   w.wyLR = w.wyRR + w.wy_cap;
   w.L1 = (double*)(b + oL1); w.R1 = (double*)(b + oR1);
   w.tmp1 = (double*)(b + oT1); w.tmp2 = (double*)(b + oT2); w.tmp3 = (double*)(b + oT3);
+  w.U2w = (double*)(b + oU2w);
   w.small = (double*)(b + oSmall);
   w.flags = (int*)(b + oFlags);
   w.exps = (int*)(b + oExps);
@@ -95,6 +105,13 @@ int alloc_work(PoolEntry* e, int n, int nb) {
   w.err = (int*)(misc + 16);
   w.status = (PanelStatus*)(misc + 64);
   w.epoch_host = 1;
+  w.ptime = nullptr;
+  w.Xinv = (double*)(b + oXinv);
+  w.safe = (int*)(b + oSafe);
+  w.xmax = (double*)(b + oXmax);
+  w.wpart = (double*)(b + oWpart);
+  w.tstore = (double*)(b + oTst);
+  e->pt_dev = (unsigned long long*)(b + oPt);
   e->base = base;
   if (cudaMallocHost((void**)&e->host_status, sizeof(PanelStatus)) != cudaSuccess) {
     cudaFree(base);
@@ -126,6 +143,56 @@ void release(PoolEntry* e) {
   e->busy = false;
 }
 
+// Optional per-launch timing by class (ht_options.profile): an event pair
+// around each launch, resolved after the stream is synchronised.
+struct Prof {
+  bool on = false;
+  cudaStream_t st = nullptr;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  std::vector<cudaEvent_t> pool;
+  double ms[HT_NCLASS] = {};
+  double flops[HT_NCLASS] = {};
+  long long launches[HT_NCLASS] = {};
+  cudaEvent_t get() {
+    if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  int cls = 0;
+  cudaEvent_t cur = nullptr;
+  void begin(int c) {
+    cls = c;
+    if (!on) return;
+    cur = get();
+    cudaEventRecord(cur, st);
+  }
+  void end(double fl) {
+    flops[cls] += fl;
+    launches[cls] += 1;
+    if (!on) return;
+    cudaEvent_t e = get();
+    cudaEventRecord(e, st);
+    pending.push_back({cls, {cur, e}});
+  }
+  void resolve() {
+    if (!on) return;
+    cudaStreamSynchronize(st);
+    for (auto& p : pending) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, p.second.first, p.second.second);
+      ms[p.first] += t;
+      pool.push_back(p.second.first);
+      pool.push_back(p.second.second);
+    }
+    pending.clear();
+  }
+  ~Prof() {
+    for (auto& p : pending) { cudaEventDestroy(p.second.first); cudaEventDestroy(p.second.second); }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
 struct Ctx {
   HtWork* w;
   cudaStream_t st;
@@ -134,13 +201,63 @@ struct Ctx {
   long lda, ldb, ldq, ldz;
   int want_qz;
   double flops;
+  Prof* prof;
 };
+
+// Launch `expr` as one timed launch of class `cls` with `fl` algorithmic flops.
+#define LAUNCH(cls, fl, expr)            \
+  do {                                   \
+    c.prof->begin(cls);                  \
+    cudaError_t e_ = (expr);             \
+    if (e_ != cudaSuccess) return e_;    \
+    c.prof->end(fl);                     \
+    c.flops += (fl);                     \
+  } while (0)
 
 #define CK(call)                         \
   do {                                   \
     cudaError_t e_ = (call);             \
     if (e_ != cudaSuccess) return e_;    \
   } while (0)
+
+// Flop counts of the launches (the algorithmic work each performs).
+double fl_gemm(double M, double N, double K) { return 2.0 * M * N * K; }
+double fl_window(double w, double k) { return 2.0 * w * k * k - 2.0 / 3.0 * k * k * k + 2.0 * w * k * k; }
+double fl_chain(int p, int k) {  // one chain; both chains have the same windows
+  double f = 0.0;
+  for (int i = 0; i < ht_num_windows(p, k); ++i) {
+    int r0, r1;
+    ht_ql_window(p, k, i, &r0, &r1);
+    f += fl_window(r1 - r0, k);
+  }
+  return f;
+}
+// right sweep of chain `mode` over `rows` rows; limit_base >= 0 clips rows to the structural bound
+double fl_sweep(int mode, int p, int k, int nwin, double lines, int limit_base, bool left) {
+  double f = 0.0;
+  for (int t = 0; t < nwin; ++t) {
+    int w = 0, kr = 0, lim = 0;
+    if (mode == 0) { int a, b; ht_ql_window(p, k, t, &a, &b); w = b - a; kr = k; lim = b; }
+    else if (mode == 1) { int a, b; ht_qr_window(p, k, t, &a, &b); w = b - a; kr = k; lim = a; }
+    else if (mode == 2) {
+      const int nbr = ht_num_right_blocks(p, k), bb = nbr - 1 - t;
+      int c0, c1, d0, d1;
+      ht_right_block(p, k, bb - 1, &c0, &c1);
+      ht_right_block(p, k, bb, &d0, &d1);
+      w = d1 - c0; kr = d1 - d0; lim = d0;
+    } else {
+      const int nlb = ht_num_left_blocks(p, k);
+      int r0, r1, e0, e1;
+      ht_left_block(p, k, t, &r0, &r1);
+      if (t + 1 < nlb) ht_left_block(p, k, t + 1, &e0, &e1); else e1 = r1;
+      w = e1 - r0; kr = r1 - r0; lim = r1;
+    }
+    double L = lines;
+    if (limit_base >= 0) L = left ? std::max(0.0, lines - (double)lim) : std::min(lines, (double)(limit_base + lim));
+    f += 4.0 * L * w * kr;
+  }
+  return f;
+}
 
 // Absorption of k right and k left reflectors (Sec. 3.3.1 and 3.3.2).
 cudaError_t absorb(Ctx& c, int s, int k) {
@@ -155,45 +272,62 @@ cudaError_t absorb(Ctx& c, int s, int k) {
   const long wst = 4L * k * k;  // WY store stride of this absorption
 
   // Remark 3.1: rows 0..s of Y = A V T, from the unmodified rows 0..s of A
-  CK(ht_gemm(st, 'N', 'N', s + 1, k, m, 1.0, A + (size_t)(s + 1) * lda, lda, V, n, 0.0, w.tmp1, n));
-  CK(ht_gemm(st, 'N', 'N', s + 1, k, k, 1.0, w.tmp1, n, w.T, nb, 0.0, w.Y, n));
-  c.flops += 2.0 * (s + 1) * k * (m + k);
+  const size_t wsd = (size_t)n * 2 * nb;  // split-K partials live in tmp2
+  LAUNCH(HT_CLASS_GEMM, fl_gemm(s + 1, k, m),
+         ht_gemm_ws(st, 'N', 'N', s + 1, k, m, 1.0, A + (size_t)(s + 1) * lda, lda, V, n, 0.0, w.tmp1, n, w.tmp2, wsd));
+  LAUNCH(HT_CLASS_GEMM, fl_gemm(s + 1, k, k), ht_gemm(st, 'N', 'N', s + 1, k, k, 1.0, w.tmp1, n, w.T, nb, 0.0, w.Y, n));
 
   // ---- right reflectors, Sec. 3.3.1 ----
   // deferred rows 0..s of the panel columns s+1..j-1, then column j (step e2)
-  if (k > 1) CK(ht_gemm(st, 'N', 'T', s + 1, k - 1, k, -1.0, w.Y, n, V, n, 1.0, A + (size_t)(s + 1) * lda, lda));
-  CK(ht_gemm(st, 'N', 'T', n, 1, k, -1.0, w.Y, n, V + (k - 1), n, 1.0, A + (size_t)j * lda, lda));
-  // (b) V2 = Q^_1 .. Q^_r L^  (eq. (5))
+  if (k > 1)
+    LAUNCH(HT_CLASS_GEMM, fl_gemm(s + 1, k - 1, k),
+           ht_gemm(st, 'N', 'T', s + 1, k - 1, k, -1.0, w.Y, n, V, n, 1.0, A + (size_t)(s + 1) * lda, lda));
+  LAUNCH(HT_CLASS_GEMM, fl_gemm(n, 1, k),
+         ht_gemm(st, 'N', 'T', n, 1, k, -1.0, w.Y, n, V + (k - 1), n, 1.0, A + (size_t)j * lda, lda));
+  // (b) V2 = Q^_1 .. Q^_r L^ (eq. (5)) and, concurrently, U2 = Q~_1 .. Q~_r R~
+  // (eq. (7), Sec. 3.3.2b) on a copy of U2 (the spike update needs U2 itself)
   const int nwr = ht_num_windows(p, k);
-  CK(ht_launch_factor_chain(st, 0, V + k, n, p, k, w.wyR, wst, w.L1));
+  LAUNCH(HT_CLASS_OTHER, 0.0,
+         cudaMemcpy2DAsync(w.U2w, n * sizeof(double), U + k, n * sizeof(double), p * sizeof(double), k,
+                           cudaMemcpyDeviceToDevice, st));
+  LAUNCH(HT_CLASS_CHAIN_FACTOR, 2.0 * fl_chain(p, k),
+         ht_launch_chains(st, V + k, w.U2w, n, p, k, w.wyR, w.wyL, wst, w.L1, w.R1));
   // (c)-(e) step 1: B, Z, A columns j+1..n-1 times the chain
-  CK(ht_sweep(st, 1, B, ldb, 0, n, j + 1, w.wyR, wst, 0, p, k, 0, nwr, 1, j + 1));
-  if (c.want_qz) CK(ht_sweep(st, 1, Z, ldz, 0, n, j + 1, w.wyR, wst, 0, p, k, 0, nwr, 0, 0));
-  CK(ht_sweep(st, 1, A, lda, 0, n, j + 1, w.wyR, wst, 0, p, k, 0, nwr, 0, 0));
-  c.flops += 4.0 * dn * p * k * 2.0 * (c.want_qz ? 3 : 2);
+  LAUNCH(HT_CLASS_SWEEP, fl_sweep(0, p, k, nwr, n, j + 1, false),
+         ht_sweep(st, 1, B, ldb, 0, n, j + 1, w.wyR, wst, 0, p, k, 0, nwr, 1, j + 1));
+  if (c.want_qz)
+    LAUNCH(HT_CLASS_SWEEP, fl_sweep(0, p, k, nwr, n, -1, false),
+           ht_sweep(st, 1, Z, ldz, 0, n, j + 1, w.wyR, wst, 0, p, k, 0, nwr, 0, 0));
+  LAUNCH(HT_CLASS_SWEEP, fl_sweep(0, p, k, nwr, n, -1, false),
+         ht_sweep(st, 1, A, lda, 0, n, j + 1, w.wyR, wst, 0, p, k, 0, nwr, 0, 0));
   // (c)/(d) steps 2-4 and (e) step 3
-  CK(ht_launch_rankk_right(st, B, ldb, n, s + 1, n - k, k, V, n, w.L1, k, w.T, nb));
-  if (c.want_qz) CK(ht_launch_rankk_right(st, Z, ldz, n, s + 1, n - k, k, V, n, w.L1, k, w.T, nb));
-  CK(ht_gemm(st, 'N', 'T', n, k, k, -1.0, w.Y, n, w.L1, k, 1.0, A + (size_t)(n - k) * lda, lda));
-  c.flops += (c.want_qz ? 2 : 1) * 8.0 * dn * k * k + 2.0 * dn * k * k;
-  // partial restore: RQ chain bottom to top (Sec. 3.3.1e)
+  const double fl_rk = dn * (4.0 * k * k + 6.0 * k * k);
+  LAUNCH(HT_CLASS_RANKK, fl_rk, ht_launch_rankk_right(st, B, ldb, n, s + 1, n - k, k, V, n, w.L1, k, w.T, nb));
+  if (c.want_qz)
+    LAUNCH(HT_CLASS_RANKK, fl_rk, ht_launch_rankk_right(st, Z, ldz, n, s + 1, n - k, k, V, n, w.L1, k, w.T, nb));
+  LAUNCH(HT_CLASS_GEMM, fl_gemm(n, k, k),
+         ht_gemm(st, 'N', 'T', n, k, k, -1.0, w.Y, n, w.L1, k, 1.0, A + (size_t)(n - k) * lda, lda));
+  // partial restore: RQ chain bottom to top (Sec. 3.3.1e), one cooperative launch
   const int nbr = ht_num_right_blocks(p, k);
-  for (int t = 0; t + 1 < nbr; ++t) {
-    const int bb = nbr - 1 - t;
-    int c0, c1, d0, d1;
-    ht_right_block(p, k, bb - 1, &c0, &c1);
-    ht_right_block(p, k, bb, &d0, &d1);
-    const int rows = d1 - d0, width = d1 - c0;
-    double* blk = B + (size_t)(j + 1 + d0) + (size_t)(j + 1 + c0) * ldb;
-    double* wy = w.wyRR + (size_t)t * wst;
-    CK(ht_launch_factor_block(st, 2, blk, ldb, rows, width, wy, wst));
-    CK(ht_apply_single(st, 1, B, ldb, 0, j + 1 + d0, j + 1 + c0, width, rows, wy, wst));
-    c.flops += 4.0 * (j + 1 + d0) * width * rows;
+  {
+    double fl = 0.0;
+    for (int t = 0; t + 1 < nbr; ++t) {
+      const int bb = nbr - 1 - t;
+      int c0, c1, d0, d1;
+      ht_right_block(p, k, bb - 1, &c0, &c1);
+      ht_right_block(p, k, bb, &d0, &d1);
+      fl += fl_window(d1 - c0, d1 - d0) + 4.0 * (j + 1 + d0) * (d1 - c0) * (d1 - d0);
+    }
+    if (nbr > 1) LAUNCH(HT_CLASS_RESTORE, fl, ht_launch_restore(st, 2, p, k, j, n, B, ldb, w.wyRR, wst, w.tstore, w.ptime));
   }
   if (nbr > 1) {
-    CK(ht_sweep(st, 1, A, lda, 0, n, j + 1, w.wyRR, wst, 2, p, k, 0, nbr - 1, 0, 0));
-    if (c.want_qz) CK(ht_sweep(st, 1, Z, ldz, 0, n, j + 1, w.wyRR, wst, 2, p, k, 0, nbr - 1, 0, 0));
-    c.flops += 4.0 * dn * p * k * 2.0 * (c.want_qz ? 2 : 1);
+    LAUNCH(HT_CLASS_SWEEP, fl_sweep(2, p, k, nbr - 1, j + 1, -1, false),
+           ht_sweep(st, 1, B, ldb, 0, j + 1, j + 1, w.wyRR, wst, 2, p, k, 0, nbr - 1, 0, 0));
+    LAUNCH(HT_CLASS_SWEEP, fl_sweep(2, p, k, nbr - 1, n, -1, false),
+           ht_sweep(st, 1, A, lda, 0, n, j + 1, w.wyRR, wst, 2, p, k, 0, nbr - 1, 0, 0));
+    if (c.want_qz)
+      LAUNCH(HT_CLASS_SWEEP, fl_sweep(2, p, k, nbr - 1, n, -1, false),
+             ht_sweep(st, 1, Z, ldz, 0, n, j + 1, w.wyRR, wst, 2, p, k, 0, nbr - 1, 0, 0));
   }
 
   // ---- left reflectors, Sec. 3.3.2 ----
@@ -201,47 +335,52 @@ cudaError_t absorb(Ctx& c, int s, int k) {
   double* sm0 = w.small;
   double* sm1 = w.small + 2 * HT_NB_MAX * HT_NB_MAX;
   double* Bsp = B + (size_t)(s + 1) + (size_t)(s + 1) * ldb;
-  CK(ht_gemm(st, 'T', 'N', k, k, m, 1.0, U, n, Bsp, ldb, 0.0, sm0, k));
-  CK(ht_gemm(st, 'T', 'N', k, k, k, 1.0, w.S, nb, sm0, k, 0.0, sm1, k));
-  CK(ht_gemm(st, 'N', 'N', k, k, k, -1.0, U, n, sm1, k, 1.0, Bsp, ldb));
-  CK(ht_launch_zero(st, B + (size_t)(j + 1) + (size_t)(s + 1) * ldb, ldb, p, k, 0));
-  CK(ht_launch_zero(st, Bsp, ldb, k, k, 1));
-  c.flops += 2.0 * k * k * (m + 2 * k);
-  // (b) U2 = Q~_1 .. Q~_r R~ (eq. (7))
+  LAUNCH(HT_CLASS_GEMM, fl_gemm(k, k, m),
+         ht_gemm_ws(st, 'T', 'N', k, k, m, 1.0, U, n, Bsp, ldb, 0.0, sm0, k, w.tmp2, wsd));
+  LAUNCH(HT_CLASS_GEMM, fl_gemm(k, k, k), ht_gemm(st, 'T', 'N', k, k, k, 1.0, w.S, nb, sm0, k, 0.0, sm1, k));
+  LAUNCH(HT_CLASS_GEMM, fl_gemm(k, k, k), ht_gemm(st, 'N', 'N', k, k, k, -1.0, U, n, sm1, k, 1.0, Bsp, ldb));
+  LAUNCH(HT_CLASS_OTHER, 0.0, ht_launch_zero(st, B + (size_t)(j + 1) + (size_t)(s + 1) * ldb, ldb, p, k, 0));
+  LAUNCH(HT_CLASS_OTHER, 0.0, ht_launch_zero(st, Bsp, ldb, k, k, 1));
   const int nwl = ht_num_windows(p, k);
-  CK(ht_launch_factor_chain(st, 1, U + k, n, p, k, w.wyL, wst, w.R1));
   // (c) step 3, (e) step 1, (d) step 1
-  CK(ht_sweep(st, 0, B, ldb, j + 1, p, j + 1, w.wyL, wst, 1, p, k, 0, nwl, 1, j + 1));
-  CK(ht_sweep(st, 0, A, lda, j, n - j, j + 1, w.wyL, wst, 1, p, k, 0, nwl, 0, 0));
-  if (c.want_qz) CK(ht_sweep(st, 1, Q, ldq, 0, n, j + 1, w.wyL, wst, 1, p, k, 0, nwl, 0, 0));
-  c.flops += 4.0 * p * k * 2.0 * (0.5 * p + (n - j) + (c.want_qz ? dn : 0.0));
+  LAUNCH(HT_CLASS_SWEEP, fl_sweep(1, p, k, nwl, p, 0, true),
+         ht_sweep(st, 0, B, ldb, j + 1, p, j + 1, w.wyL, wst, 1, p, k, 0, nwl, 1, j + 1));
+  LAUNCH(HT_CLASS_SWEEP, fl_sweep(1, p, k, nwl, n - j, -1, true),
+         ht_sweep(st, 0, A, lda, j, n - j, j + 1, w.wyL, wst, 1, p, k, 0, nwl, 0, 0));
+  if (c.want_qz)
+    LAUNCH(HT_CLASS_SWEEP, fl_sweep(1, p, k, nwl, n, -1, false),
+           ht_sweep(st, 1, Q, ldq, 0, n, j + 1, w.wyL, wst, 1, p, k, 0, nwl, 0, 0));
   // U~ = [U1; R~1] (2k x k) in tmp3 with ld 2k
   double* Ut = w.tmp3;
-  CK(cudaMemcpy2DAsync(Ut, 2 * k * sizeof(double), U, n * sizeof(double), k * sizeof(double), k,
-                       cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpy2DAsync(Ut + k, 2 * k * sizeof(double), w.R1, k * sizeof(double), k * sizeof(double), k,
-                       cudaMemcpyDeviceToDevice, st));
+  LAUNCH(HT_CLASS_OTHER, 0.0,
+         cudaMemcpy2DAsync(Ut, 2 * k * sizeof(double), U, n * sizeof(double), k * sizeof(double), k,
+                           cudaMemcpyDeviceToDevice, st));
+  LAUNCH(HT_CLASS_OTHER, 0.0,
+         cudaMemcpy2DAsync(Ut + k, 2 * k * sizeof(double), w.R1, k * sizeof(double), k * sizeof(double), k,
+                           cudaMemcpyDeviceToDevice, st));
   // (c) steps 4-5, (e) steps 2-3, (d) steps 2-3
-  CK(ht_rankk_left(st, B, ldb, j + 1, p, s + 1, 2 * k, k, Ut, 2 * k, w.S, nb));
-  CK(ht_rankk_left(st, A, lda, j, n - j, s + 1, 2 * k, k, Ut, 2 * k, w.S, nb));
-  if (c.want_qz) CK(ht_rankk_right_w(st, Q, ldq, n, s + 1, 2 * k, k, Ut, 2 * k, w.S, nb));
-  c.flops += 8.0 * k * k * (p + (n - j) + (c.want_qz ? dn : 0.0));
-  // (f) restore: QR chain top to bottom
+  const double fl_rkl = 8.0 * k * k + 2.0 * k * k;
+  LAUNCH(HT_CLASS_RANKK, fl_rkl * p, ht_rankk_left(st, B, ldb, j + 1, p, s + 1, 2 * k, k, Ut, 2 * k, w.S, nb));
+  LAUNCH(HT_CLASS_RANKK, fl_rkl * (n - j), ht_rankk_left(st, A, lda, j, n - j, s + 1, 2 * k, k, Ut, 2 * k, w.S, nb));
+  if (c.want_qz)
+    LAUNCH(HT_CLASS_RANKK, fl_rkl * dn, ht_rankk_right_w(st, Q, ldq, n, s + 1, 2 * k, k, Ut, 2 * k, w.S, nb));
+  // (f) restore: QR chain top to bottom, one cooperative launch
   const int nlb = ht_num_left_blocks(p, k);
-  for (int t = 0; t < nlb; ++t) {
-    int r0, r1, e0, e1;
-    ht_left_block(p, k, t, &r0, &r1);
-    if (t + 1 < nlb) ht_left_block(p, k, t + 1, &e0, &e1); else e1 = r1;
-    const int width = e1 - r0, kc = r1 - r0;
-    double* blk = B + (size_t)(j + 1 + r0) + (size_t)(j + 1 + r0) * ldb;
-    double* wy = w.wyLR + (size_t)t * wst;
-    CK(ht_launch_factor_block(st, 3, blk, ldb, width, kc, wy, wst));
-    CK(ht_apply_single(st, 0, B, ldb, j + 1 + r1, n - (j + 1 + r1), j + 1 + r0, width, kc, wy, wst));
-    c.flops += 4.0 * (n - (j + 1 + r1)) * width * kc;
+  {
+    double fl = 0.0;
+    for (int t = 0; t < nlb; ++t) {
+      int r0, r1, e0, e1;
+      ht_left_block(p, k, t, &r0, &r1);
+      if (t + 1 < nlb) ht_left_block(p, k, t + 1, &e0, &e1); else e1 = r1;
+      fl += fl_window(e1 - r0, r1 - r0) + 4.0 * (n - (j + 1 + r1)) * (e1 - r0) * (r1 - r0);
+    }
+    LAUNCH(HT_CLASS_RESTORE, fl, ht_launch_restore(st, 3, p, k, j, n, B, ldb, w.wyLR, wst, w.tstore, w.ptime));
   }
-  CK(ht_sweep(st, 0, A, lda, j, n - j, j + 1, w.wyLR, wst, 3, p, k, 0, nlb, 0, 0));
-  if (c.want_qz) CK(ht_sweep(st, 1, Q, ldq, 0, n, j + 1, w.wyLR, wst, 3, p, k, 0, nlb, 0, 0));
-  c.flops += 4.0 * p * k * 2.0 * ((n - j) + (c.want_qz ? dn : 0.0));
+  LAUNCH(HT_CLASS_SWEEP, fl_sweep(3, p, k, nlb, n - j, -1, true),
+         ht_sweep(st, 0, A, lda, j, n - j, j + 1, w.wyLR, wst, 3, p, k, 0, nlb, 0, 0));
+  if (c.want_qz)
+    LAUNCH(HT_CLASS_SWEEP, fl_sweep(3, p, k, nlb, n, -1, false),
+           ht_sweep(st, 1, Q, ldq, 0, n, j + 1, w.wyLR, wst, 3, p, k, 0, nlb, 0, 0));
   return cudaGetLastError();
 }
 
@@ -293,7 +432,12 @@ int reduce_impl(int n, double* A, int lda, double* B, int ldb, double* Q, int ld
   if (!pe) return rc;
   HtWork& w = pe->w;
   w.stream = st;
-  Ctx c{&w, st, n, A, B, Q, Z, lda, ldb, ldq, ldz, want_qz, 0.0};
+  Prof prof;
+  prof.on = (opt && opt->profile);
+  w.ptime = prof.on ? pe->pt_dev : nullptr;
+  if (prof.on) cudaMemsetAsync(pe->pt_dev, 0, 32 * sizeof(unsigned long long), st);
+  prof.st = st;
+  Ctx c{&w, st, n, A, B, Q, Z, lda, ldb, ldq, ldz, want_qz, 0.0, &prof};
   cudaEvent_t ev[4] = {};
   const bool timing = (stats != nullptr);
   if (timing)
@@ -317,7 +461,9 @@ int reduce_impl(int n, double* A, int lda, double* B, int ldb, double* Q, int ld
       if (cudaMemsetAsync(w.status, 0, sizeof(PanelStatus), st) != cudaSuccess) { result = HT_ERR_CUDA; break; }
       if (ht_launch_prepare_B(w, B, ldb, s, seed, 0) != cudaSuccess) { result = HT_ERR_CUDA; break; }
       if (timing) cudaEventRecord(ev[0], st);
+      prof.begin(HT_CLASS_PANEL);
       cudaError_t e = ht_launch_panel(w, A, lda, B, ldb, s, kmax, tol_scale, max_ir);
+      prof.end(0.0);
       if (e != cudaSuccess) {
         std::fprintf(stderr, "libht: panel launch failed: %s\n", cudaGetErrorString(e));
         result = HT_ERR_CUDA;
@@ -334,6 +480,16 @@ int reduce_impl(int n, double* A, int lda, double* B, int ldb, double* Q, int ld
       if (ps.error != 0) { result = ps.error; break; }
       int k = ps.k_done;
       if (k < 1) { result = HT_ERR_INTERNAL; break; }
+      {
+        // panel flops: per column the Y GEMV (2 m p) and the solve and residual
+        // passes over the triangle of B (m^2 each), plus m^2 per correction
+        const int m = n - s - 1;
+        double fl = 0.0;
+        for (int q = 0; q < k; ++q) fl += 2.0 * (double)m * (m - q) + 2.0 * (double)m * m;
+        fl += 2.0 * (double)m * m * ps.ir_steps;
+        prof.flops[HT_CLASS_PANEL] += fl;
+        c.flops += fl;
+      }
       if (stats) {
         stats->panels += 1;
         stats->early_absorptions += ps.failed;
@@ -343,15 +499,6 @@ int reduce_impl(int n, double* A, int lda, double* B, int ldb, double* Q, int ld
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev[0], ev[1]);
         stats->ms_panel += ms;
-      }
-      {
-        const int m = n - s - 1;
-        // panel flops: per column the Y GEMV (2 m p), solve and residual (~m^2 each), plus corrections
-        for (int q = 0; q < k; ++q) {
-          const double mm = m, pp = m - q;
-          c.flops += 2.0 * mm * pp + 2.0 * mm * mm;
-        }
-        c.flops += 2.0 * (double)m * m * ps.ir_steps;
       }
       if (timing) cudaEventRecord(ev[2], st);
       e = absorb(c, s, k);
@@ -367,6 +514,7 @@ int reduce_impl(int n, double* A, int lda, double* B, int ldb, double* Q, int ld
         cudaEventElapsedTime(&ms, ev[2], ev[3]);
         stats->ms_absorb += ms;
       }
+      prof.resolve();
       s += k;
     }
     if (result != HT_OK) break;
@@ -378,7 +526,20 @@ int reduce_impl(int n, double* A, int lda, double* B, int ldb, double* Q, int ld
     }
     if (derr != 0) result = derr;
   } while (0);
-  if (stats) stats->flops_nominal = c.flops;
+  prof.resolve();
+  if (stats && prof.on) {
+    unsigned long long pt[24];
+    cudaMemcpy(pt, pe->pt_dev, sizeof(pt), cudaMemcpyDeviceToHost);
+    for (int q = 0; q < 24; ++q) stats->panel_phase_ms[q] = pt[q] * 1e-6;
+  }
+  if (stats) {
+    stats->flops_nominal = c.flops;
+    for (int q = 0; q < HT_NCLASS; ++q) {
+      stats->ms_by_class[q] = prof.ms[q];
+      stats->flops_by_class[q] = prof.flops[q];
+      stats->launches_by_class[q] = prof.launches[q];
+    }
+  }
   if (timing)
     for (auto& e : ev) cudaEventDestroy(e);
   {
@@ -429,14 +590,17 @@ int ht_last_device_status(ht_stream_t stream, int* status) {
 
 int ht_finalize(void) {
   std::lock_guard<std::mutex> lk(g_pool_mu);
+  std::vector<PoolEntry*> keep;
   for (PoolEntry* e : g_pool) {
-    if (e->busy) continue;
+    if (e->busy) {
+      keep.push_back(e);
+      continue;
+    }
     cudaFree(e->base);
     cudaFreeHost(e->host_status);
     delete e;
   }
-  g_pool.erase(std::remove_if(g_pool.begin(), g_pool.end(), [](PoolEntry* e) { return !e->busy ? true : false; }),
-               g_pool.end());
+  g_pool.swap(keep);
   return HT_OK;
 }
 

@@ -14,6 +14,8 @@
 //               spike update of Sec. 3.3.2c step 1).
 // Window geometry is recomputed on the device from (p, k) with the same
 // functions the host uses (ht_common.cuh), so no descriptors are copied.
+#include <algorithm>
+
 #include "ht_common.cuh"
 
 namespace {
@@ -259,27 +261,30 @@ __global__ void __launch_bounds__(HT_THREADS) rankk_left_kernel(double* X, long 
 
 // C = alpha op(A) op(B) + beta C, 64 x 64 tiles, 4 x 4 per thread, K chunks of 16.
 constexpr int GT = 64, GK = 16;
+// With gridDim.z > 1 (split K) each z-slice writes alpha * (its partial
+// product) to part + z * M * N (ld M); a second kernel adds the slices in order.
 __global__ void __launch_bounds__(256) gemm_kernel(int ta, int tb, int M, int N, int K, double alpha,
                                                    const double* A, long lda, const double* Bm, long ldb,
-                                                   double beta, double* C, long ldc) {
+                                                   double beta, double* C, long ldc, double* part, int kchunk) {
   __shared__ double As[GK][GT + 1];
   __shared__ double Bs[GK][GT + 1];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int m0 = blockIdx.x * GT, n0 = blockIdx.y * GT;
   double acc[4][4] = {};
-  for (int k0 = 0; k0 < K; k0 += GK) {
+  const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
+  for (int k0 = kbeg; k0 < kend; k0 += GK) {
     for (int e = threadIdx.x; e < GK * GT; e += 256) {
       const int kk = e % GK, mm = e / GK;
       const int gm = m0 + mm, gk = k0 + kk;
       double v = 0.0;
-      if (gm < M && gk < K) v = ta ? A[(size_t)gk + (size_t)gm * lda] : A[(size_t)gm + (size_t)gk * lda];
+      if (gm < M && gk < kend) v = ta ? A[(size_t)gk + (size_t)gm * lda] : A[(size_t)gm + (size_t)gk * lda];
       As[kk][mm] = v;
     }
     for (int e = threadIdx.x; e < GK * GT; e += 256) {
       const int kk = e % GK, nn = e / GK;
       const int gn = n0 + nn, gk = k0 + kk;
       double v = 0.0;
-      if (gn < N && gk < K) v = tb ? Bm[(size_t)gn + (size_t)gk * ldb] : Bm[(size_t)gk + (size_t)gn * ldb];
+      if (gn < N && gk < kend) v = tb ? Bm[(size_t)gn + (size_t)gk * ldb] : Bm[(size_t)gk + (size_t)gn * ldb];
       Bs[kk][nn] = v;
     }
     __syncthreads();
@@ -303,10 +308,26 @@ __global__ void __launch_bounds__(256) gemm_kernel(int ta, int tb, int M, int N,
     for (int jx = 0; jx < 4; ++jx) {
       const int gm = m0 + tx + 16 * i, gn = n0 + ty + 16 * jx;
       if (gm < M && gn < N) {
-        double* c = C + (size_t)gm + (size_t)gn * ldc;
-        *c = alpha * acc[i][jx] + (beta == 0.0 ? 0.0 : beta * (*c));
+        if (part) {
+          part[(size_t)blockIdx.z * M * N + gm + (size_t)gn * M] = alpha * acc[i][jx];
+        } else {
+          double* c = C + (size_t)gm + (size_t)gn * ldc;
+          *c = alpha * acc[i][jx] + (beta == 0.0 ? 0.0 : beta * (*c));
+        }
       }
     }
+}
+
+__global__ void splitk_reduce_kernel(int M, int N, int splits, const double* part, double beta, double* C,
+                                     long ldc) {
+  const long total = (long)M * N;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int z = 0; z < splits; ++z) v += part[(size_t)z * total + e];
+    const int gm = (int)(e % M), gn = (int)(e / M);
+    double* c = C + (size_t)gm + (size_t)gn * ldc;
+    *c = v + (beta == 0.0 ? 0.0 : beta * (*c));
+  }
 }
 
 __global__ void zero_kernel(double* X, long ldx, int rows, int cols, int lower_only) {
@@ -345,12 +366,34 @@ inline int grid_for(long work, int per) {
 
 }  // namespace
 
+cudaError_t ht_gemm_ws(cudaStream_t st, char ta, char tb, int M, int N, int K, double alpha, const double* A,
+                       int lda, const double* Bm, int ldb, double beta, double* C, int ldc, double* ws,
+                       size_t ws_doubles) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  dim3 grid((M + GT - 1) / GT, (N + GT - 1) / GT, 1);
+  const long tiles = (long)grid.x * grid.y;
+  int splits = 1;
+  if (ws && tiles < 2 * 152 && K > 4 * GK) {
+    splits = (int)std::min<long>((2 * 152 + tiles - 1) / tiles, (K + 4 * GK - 1) / (4 * GK));
+    while (splits > 1 && (size_t)splits * M * N > ws_doubles) --splits;
+  }
+  if (splits <= 1) {
+    gemm_kernel<<<grid, 256, 0, st>>>(ta == 'T', tb == 'T', M, N, K, alpha, A, lda, Bm, ldb, beta, C, ldc, nullptr,
+                                      K);
+    return cudaGetLastError();
+  }
+  int kchunk = (K + splits - 1) / splits;
+  kchunk = (kchunk + GK - 1) / GK * GK;
+  splits = (K + kchunk - 1) / kchunk;
+  grid.z = splits;
+  gemm_kernel<<<grid, 256, 0, st>>>(ta == 'T', tb == 'T', M, N, K, alpha, A, lda, Bm, ldb, beta, C, ldc, ws, kchunk);
+  splitk_reduce_kernel<<<grid_for((long)M * N, 256), 256, 0, st>>>(M, N, splits, ws, beta, C, ldc);
+  return cudaGetLastError();
+}
+
 cudaError_t ht_gemm(cudaStream_t st, char ta, char tb, int M, int N, int K, double alpha, const double* A, int lda,
                     const double* Bm, int ldb, double beta, double* C, int ldc) {
-  if (M <= 0 || N <= 0) return cudaSuccess;
-  dim3 grid((M + GT - 1) / GT, (N + GT - 1) / GT);
-  gemm_kernel<<<grid, 256, 0, st>>>(ta == 'T', tb == 'T', M, N, K, alpha, A, lda, Bm, ldb, beta, C, ldc);
-  return cudaGetLastError();
+  return ht_gemm_ws(st, ta, tb, M, N, K, alpha, A, lda, Bm, ldb, beta, C, ldc, nullptr, 0);
 }
 
 static cudaError_t launch_sweep(cudaStream_t st, bool right, SweepArgs a) {

@@ -16,7 +16,8 @@
 #include "../../include/ht.h"
 
 #define HT_THREADS 256
-#define HT_TRSV_BS 64          // row block of the triangular solve / multiply
+#define HT_TRSV_BS 64          // row tile of the triangular solve / multiply
+#define HT_TRSV_BI 256         // diagonal block of the grid-synchronous solve (explicit inverses)
 #define HT_NB_MAX 64           // largest panel width (windows live in shared memory)
 #define HT_BIG_EXP 500         // rescale threshold 2^500 of the scaled solve
 #define HT_SPIN_LIMIT (1 << 22)  // ~ a few seconds of polling, then HT_ERR_TIMEOUT
@@ -122,6 +123,12 @@ struct HtWork {
   double *small;           // nb x nb scratch (4 of them)
   int *err;                // device error word
   unsigned epoch_host;     // next TRSV epoch (host shadow)
+  unsigned long long* ptime;  // per-phase panel timers (profile mode) or null
+  double* Xinv;            // inverses of the diagonal blocks of the trailing B (n x HT_TRSV_BI)
+  int* safe;               // per diagonal block: inverse usable
+  double* xmax;            // per-CTA max |x| partials
+  double* wpart;           // chunk partials of the triangular multiply
+  double* tstore;          // T factors of the restore steps (HT_NB_MAX^2 each)
   cudaStream_t stream;
 };
 #define HT_PART_STRIDE 80   // >= nb + 8 for nb <= 64 ... plus norms
@@ -135,10 +142,16 @@ cudaError_t ht_launch_panel(HtWork& w, double* A, int lda, const double* B, int 
                             double tol_scale, int max_ir);
 cudaError_t ht_gemm(cudaStream_t st, char ta, char tb, int M, int N, int K, double alpha, const double* A, int lda,
                     const double* Bm, int ldb, double beta, double* C, int ldc);
-cudaError_t ht_launch_factor_chain(cudaStream_t st, int mode, double* X, int ldx, int p, int k, double* wy,
-                                   size_t stride, double* out_tri);
-cudaError_t ht_launch_factor_block(cudaStream_t st, int mode, double* X, int ldx, int rows, int cols, double* wy,
-                                   size_t stride);
+// as ht_gemm, splitting K over extra CTAs (partials in ws) when the output has few tiles
+cudaError_t ht_gemm_ws(cudaStream_t st, char ta, char tb, int M, int N, int K, double alpha, const double* A,
+                       int lda, const double* Bm, int ldb, double beta, double* C, int ldc, double* ws,
+                       size_t ws_doubles);
+// QL chain of V2 and QR chain of U2 (two CTAs) plus the T / Ww formation of every window
+cudaError_t ht_launch_chains(cudaStream_t st, double* V2, double* U2, long ld, int p, int k, double* wyR, double* wyL,
+                             size_t stride, double* L1, double* R1);
+// restore chain of B (mode 2: RQ right, mode 3: QR left), one cooperative launch
+cudaError_t ht_launch_restore(cudaStream_t st, int mode, int p, int k, int j, int n, double* B, long ldb, double* wy,
+                              size_t stride, double* tstore, unsigned long long* ptime);
 cudaError_t ht_sweep(cudaStream_t st, int right, double* X, long ldx, int line0, int nlines, int origin,
                      const double* wy, long stride, int mode, int p, int k, int t0, int t1, int use_limit,
                      int limit_base);

@@ -1,100 +1,179 @@
 // Small Householder factorizations of the absorption (Sec. 3.3): the QL chain
 // that reduces V2 to L-hat (eq. (5)), the QR chain that reduces U2 to R-tilde
 // (eq. (7)), and the RQ / QR factorizations of the blocks of B in the restore
-// chains (Sec. 3.3.1e, 3.3.2f).  Each factorization runs on one CTA with the
-// block in shared memory and returns its orthogonal factor in regular WY form
-// G = I - Vw Ww^T, Ww = Vw T^T, with T grown by the rule of eq. (1)
-// (T <- [T, -tau T Vw^T v; 0, tau]) over the reflectors in product order.
+// chains (Sec. 3.3.1e, 3.3.2f).  Every orthogonal factor is returned in regular
+// WY form G = I - Vw Ww^T with Ww = Vw T^T, T grown by the rule of eq. (1)
+// over the reflectors in product order.
 //
-// An RQ factorization X G = [0 R1] of a k x w block is the QL factorization
-// of X^T: X^T = G [0; R1^T].
+// Launch structure
+//   chains_kernel      2 CTAs: CTA 0 runs the QL chain of V2 and CTA 1 the QR
+//                      chain of U2 (they are independent); each window's
+//                      reflector vectors and coefficients go to the WY store.
+//   form_wy_kernel     one CTA per window: T (recursive halving of eq. (1)) and
+//                      Ww = Vw T^T, off the sequential path of the chains.
+//   restore_kernel     cooperative, one launch per restore chain: CTA 0 factors
+//                      the next block of B (RQ right / QR left) and forms its WY
+//                      factors; after a grid barrier every CTA applies them to
+//                      its stripes of B; a second barrier ends the step.
+// An RQ factorization X G = [0 R1] of a k x w block is the QL factorization of
+// X^T: X^T = G [0; R1^T].
+#include <cooperative_groups.h>
+
 #include "ht_common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
 constexpr int MAXW = 2 * HT_NB_MAX;  // largest window height
 
-// Householder QR (lower=false) or QL (lower=true) of the w x kk column-major
-// matrix X (shared, ld w) in place.  On return X holds R (QR: upper triangle
-// in rows 0..kk-1) or L (QL: lower triangle in rows w-kk..w-1) with exact zeros
-// elsewhere, Vs (shared, w x kk) the reflector vectors in product order and
-// tau[q] their coefficients.
-__device__ void house_factor(double* X, int w, int kk, bool ql, double* Vs, double* tau, double* red) {
+// Householder scalars of a column with pivot x0 and squared tail norm tail
+// (DLARFG rule): beta = (alpha - x0) / alpha, alpha = -sign(x0) ||x||,
+// scal = 1 / (x0 - alpha).
+__device__ __forceinline__ void house_scalars(double x0, double tail, double* sc) {
+  if (tail == 0.0) {
+    sc[0] = 0.0; sc[1] = x0; sc[2] = 0.0;
+    return;
+  }
+  const double nr = sqrt(x0 * x0 + tail);
+  const double alpha = (x0 >= 0.0) ? -nr : nr;
+  sc[0] = (alpha - x0) / alpha;
+  sc[1] = alpha;
+  sc[2] = 1.0 / (x0 - alpha);
+}
+
+// Householder QR (ql = false) or QL (ql = true) of the w x kk column-major
+// matrix X (shared, ld w) in place.  On return X holds R (upper triangle in
+// rows 0..kk-1) or L (lower triangle in rows w-kk..w-1) with exact zeros
+// elsewhere, Vs (w x kk) the reflector vectors in product order and tau[q].
+// Two block barriers per reflector; the scalars of the next reflector are
+// computed by the single warp that updates the next column (sc[0..2]).
+__device__ void house_factor(double* X, int w, int kk, bool ql, double* Vs, double* tau, double* sc) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   for (int e = tid; e < w * kk; e += blockDim.x) Vs[e] = 0.0;
+  if (wid == 0) {
+    const int c = ql ? kk - 1 : 0, t = ql ? w - kk + c : c;
+    const int lo = ql ? 0 : t, hi = ql ? t + 1 : w;
+    double s = 0.0;
+    for (int r = lo + lane; r < hi; r += 32)
+      if (r != t) s += X[r + c * w] * X[r + c * w];
+    s = ht_warp_sum(s);
+    if (lane == 0) house_scalars(X[t + c * w], s, sc);
+  }
   __syncthreads();
   for (int q = 0; q < kk; ++q) {
-    // column c and pivot row t of this reflector
     const int c = ql ? (kk - 1 - q) : q;
     const int t = ql ? (w - kk + c) : c;
-    // rows of the reflector: QR [t, w), QL [0, t]
     const int lo = ql ? 0 : t, hi = ql ? t + 1 : w;
-    double tail = 0.0;
-    if (wid == 0) {
-      for (int r = lo + lane; r < hi; r += 32)
-        if (r != t) tail += X[r + c * w] * X[r + c * w];
-      tail = ht_warp_sum(tail);
-      if (lane == 0) {
-        const double x0 = X[t + c * w];
-        double beta, alpha, scal;
-        if (tail == 0.0) {
-          beta = 0.0; alpha = x0; scal = 0.0;
-        } else {
-          const double nrm = sqrt(x0 * x0 + tail);
-          alpha = (x0 >= 0.0) ? -nrm : nrm;
-          beta = (alpha - x0) / alpha;
-          scal = 1.0 / (x0 - alpha);
-        }
-        red[0] = beta; red[1] = alpha; red[2] = scal;
-      }
-    }
-    __syncthreads();
-    const double beta = red[0], alpha = red[1], scal = red[2];
-    // reflector vector into Vs(:, q)
+    const double beta = sc[0], alpha = sc[1], scal = sc[2];
     for (int r = lo + tid; r < hi; r += blockDim.x) Vs[r + q * w] = (r == t) ? 1.0 : X[r + c * w] * scal;
+    if (tid == 0) tau[q] = beta;
     __syncthreads();
-    // apply to the other columns still to be reduced: QR columns c+1..kk-1,
-    // QL columns 0..c-1 (rows [lo, hi))
-    if (beta != 0.0) {
-      const int cb = ql ? 0 : c + 1, ce = ql ? c : kk;
-      for (int cc = cb + wid; cc < ce; cc += nw) {
-        double d = 0.0;
-        for (int r = lo + lane; r < hi; r += 32) d += Vs[r + q * w] * X[r + cc * w];
-        d = ht_warp_sum(d) * beta;
-        for (int r = lo + lane; r < hi; r += 32) X[r + cc * w] -= d * Vs[r + q * w];
+    // update the columns still to reduce, four per warp at a time with a
+    // packed cross-lane reduction of the four dot products (6 FP64 adds
+    // instead of 20); the warp owning the next column also prepares the
+    // next reflector's scalars
+    const int cb = ql ? 0 : c + 1, ce = ql ? c : kk;
+    const int cnext = ql ? c - 1 : c + 1;
+    for (int g0 = cb + 4 * wid; g0 < ce; g0 += 4 * nw) {
+      double d[4] = {0.0, 0.0, 0.0, 0.0};
+      if (beta != 0.0) {
+        for (int r = lo + lane; r < hi; r += 32) {
+          const double vr = Vs[r + q * w];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (g0 + i < ce) d[i] += vr * X[r + (g0 + i) * w];
+        }
+        const bool b16 = lane & 16, b8 = lane & 8;
+        double s0 = b16 ? d[2] : d[0], s1 = b16 ? d[3] : d[1];
+        const double o0 = __shfl_xor_sync(0xffffffffu, b16 ? d[0] : d[2], 16);
+        const double o1 = __shfl_xor_sync(0xffffffffu, b16 ? d[1] : d[3], 16);
+        s0 += o0;
+        s1 += o1;
+        double s = b8 ? s1 : s0;
+        s += __shfl_xor_sync(0xffffffffu, b8 ? s0 : s1, 8);
+        s += __shfl_xor_sync(0xffffffffu, s, 4);
+        s += __shfl_xor_sync(0xffffffffu, s, 2);
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+        // column g0 + i sits in lanes with (b16, b8) = (i >> 1, i & 1)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) d[i] = __shfl_sync(0xffffffffu, s, 16 * (i >> 1) + 8 * (i & 1)) * beta;
+        for (int r = lo + lane; r < hi; r += 32) {
+          const double vr = Vs[r + q * w];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (g0 + i < ce) X[r + (g0 + i) * w] -= d[i] * vr;
+        }
+      }
+      if (cnext >= g0 && cnext < min(ce, g0 + 4)) {
+        const int cc = cnext;
+        const int t2 = ql ? (w - kk + cc) : cc;
+        const int lo2 = ql ? 0 : t2, hi2 = ql ? t2 + 1 : w;
+        __syncwarp();  // rows of column cc were updated by other lanes of this warp
+        double sq = 0.0;
+        for (int r = lo2 + lane; r < hi2; r += 32)
+          if (r != t2) sq += X[r + cc * w] * X[r + cc * w];
+        sq = ht_warp_sum(sq);
+        __syncwarp();
+        if (lane == 0) house_scalars(X[t2 + cc * w], sq, sc + 4);
       }
     }
-    __syncthreads();
     for (int r = lo + tid; r < hi; r += blockDim.x) X[r + c * w] = (r == t) ? alpha : 0.0;
-    if (tid == 0) tau[q] = beta;
+    __syncthreads();
+    if (tid < 3) sc[tid] = sc[4 + tid];
     __syncthreads();
   }
 }
 
-// T (kk x kk, upper, ld kk) of G = H_0 H_1 ... = I - Vs T Vs^T by the growth
-// rule of eq. (1), then Ww = Vs T^T (w x kk).  G_ = Vs^T Vs is scratch.
-__device__ void form_wy(const double* Vs, const double* tau, int w, int kk, double* Tm, double* Gm, double* Ww) {
+// T (kk x kk upper, ld kk) with Vs T Vs^T = I - H_0 H_1 ... by recursive
+// halving: T = [T1, -T1 (V1^T V2) T2; 0, T2] (eq. (1) applied blockwise).
+// Gm (kk x kk) receives V^T V; scr holds kk*kk doubles.
+__device__ void form_t(const double* Vs, const double* tau, int w, int kk, double* Tm, double* Gm, double* scr) {
   const int tid = threadIdx.x;
   for (int e = tid; e < kk * kk; e += blockDim.x) {
     const int a = e % kk, b = e / kk;
-    double d = 0.0;
-    if (a < b)
-      for (int r = 0; r < w; ++r) d += Vs[r + a * w] * Vs[r + b * w];
-    Gm[e] = d;
-    Tm[e] = 0.0;
+    double d0 = 0.0, d1 = 0.0;
+    if (a < b) {
+      int r = 0;
+      for (; r + 1 < w; r += 2) {
+        d0 += Vs[r + a * w] * Vs[r + b * w];
+        d1 += Vs[r + 1 + a * w] * Vs[r + 1 + b * w];
+      }
+      if (r < w) d0 += Vs[r + a * w] * Vs[r + b * w];
+    }
+    Gm[e] = d0 + d1;
+    Tm[e] = (a == b) ? tau[a] : 0.0;
   }
   __syncthreads();
-  for (int q = 0; q < kk; ++q) {
-    // T(0:q, q) = -tau_q T(0:q, 0:q) (Vs^T v_q)(0:q)
-    for (int i = tid; i < q; i += blockDim.x) {
-      double d = 0.0;
-      for (int l = i; l < q; ++l) d += Tm[i + l * kk] * Gm[l + q * kk];
-      Tm[i + q * kk] = -tau[q] * d;
+  for (int h = 1; h < kk; h *= 2) {
+    // pairs (lo block [p0, p0+h), hi block [p0+h, p0+2h)): T12 = -T11 (G12 T22)
+    for (int e = tid; e < kk * kk; e += blockDim.x) {
+      const int a = e % kk, b = e / kk;
+      const int p0 = (a / (2 * h)) * (2 * h);
+      const bool in = (a < p0 + h) && (b >= p0 + h) && (b < min(p0 + 2 * h, kk));
+      double v = 0.0;
+      if (in)
+        for (int l = p0 + h; l <= b; ++l) v += Gm[a + l * kk] * Tm[l + b * kk];
+      scr[e] = v;
     }
-    if (tid == 0) Tm[q + q * kk] = tau[q];
+    __syncthreads();
+    for (int e = tid; e < kk * kk; e += blockDim.x) {
+      const int a = e % kk, b = e / kk;
+      const int p0 = (a / (2 * h)) * (2 * h);
+      const bool in = (a < p0 + h) && (b >= p0 + h) && (b < min(p0 + 2 * h, kk));
+      if (in) {
+        double v = 0.0;
+        for (int l = a; l < p0 + h; ++l) v += Tm[a + l * kk] * scr[l + b * kk];
+        Tm[e] = -v;
+      }
+    }
     __syncthreads();
   }
-  for (int e = tid; e < w * kk; e += blockDim.x) {
+}
+
+// Ww = Vs T^T (w x kk, ld w).
+__device__ void form_w(const double* Vs, const double* Tm, int w, int kk, double* Ww) {
+  for (int e = threadIdx.x; e < w * kk; e += blockDim.x) {
     const int r = e % w, i = e / w;
     double d = 0.0;
     for (int l = i; l < kk; ++l) d += Vs[r + l * w] * Tm[i + l * kk];
@@ -103,85 +182,266 @@ __device__ void form_wy(const double* Vs, const double* tau, int w, int kk, doub
   __syncthreads();
 }
 
-// shared layout: X (MAXW*HT_NB_MAX), Vs (same), Tm, Gm (HT_NB_MAX^2 each), tau, red
+// shared layout: X, Vs (MAXW*HT_NB_MAX each), Tm, Gm, scr (HT_NB_MAX^2 each), tau, sc (32)
 __host__ __device__ inline size_t factor_smem_doubles() {
-  return 2 * (size_t)MAXW * HT_NB_MAX + 2 * (size_t)HT_NB_MAX * HT_NB_MAX + HT_NB_MAX + 32;
+  return 2 * (size_t)MAXW * HT_NB_MAX + 3 * (size_t)HT_NB_MAX * HT_NB_MAX + HT_NB_MAX + 32;
 }
 
-// Factor one w x kk window (QR or QL) whose rows are X0[r0 + r] (global, ld),
-// write the reduced window back, and store Vw, Ww at wy.
-__device__ void factor_window(double* Xg, long ld, int r0, int w, int kk, bool ql, double* wy, size_t stride,
-                              double* sm) {
-  double* X = sm;
-  double* Vs = X + MAXW * HT_NB_MAX;
-  double* Tm = Vs + MAXW * HT_NB_MAX;
-  double* Gm = Tm + HT_NB_MAX * HT_NB_MAX;
-  double* tau = Gm + HT_NB_MAX * HT_NB_MAX;
-  double* red = tau + HT_NB_MAX;
-  for (int e = threadIdx.x; e < w * kk; e += blockDim.x) {
-    const int r = e % w, c = e / w;
-    X[e] = Xg[(size_t)(r0 + r) + (size_t)c * ld];
-  }
-  __syncthreads();
-  house_factor(X, w, kk, ql, Vs, tau, red);
-  double* Vw = wy;
-  double* Ww = wy + ht_wy_half(stride);
-  form_wy(Vs, tau, w, kk, Tm, Gm, Ww);
-  for (int e = threadIdx.x; e < w * kk; e += blockDim.x) {
-    const int r = e % w, c = e / w;
-    Xg[(size_t)(r0 + r) + (size_t)c * ld] = X[e];
-    Vw[e] = Vs[e];
-  }
-  __syncthreads();
+struct FSm {
+  double *X, *Vs, *Tm, *Gm, *scr, *tau, *nrm;
+};
+__device__ FSm fsm(double* sm) {
+  FSm f;
+  f.X = sm;
+  f.Vs = f.X + MAXW * HT_NB_MAX;
+  f.Tm = f.Vs + MAXW * HT_NB_MAX;
+  f.Gm = f.Tm + HT_NB_MAX * HT_NB_MAX;
+  f.scr = f.Gm + HT_NB_MAX * HT_NB_MAX;
+  f.tau = f.scr + HT_NB_MAX * HT_NB_MAX;
+  f.nrm = f.tau + HT_NB_MAX;
+  return f;
 }
 
-// mode 0: QL chain on V2 (p x k) top to bottom, L-hat_1 -> tri (k x k, ld k)
-// mode 1: QR chain on U2 (p x k) bottom to top, R-tilde_1 -> tri
-__global__ void __launch_bounds__(HT_THREADS) factor_chain_kernel(int mode, double* X, long ld, int p, int k,
-                                                                   double* wy, size_t stride, double* tri) {
-  extern __shared__ double sm[];
+// QL (mode 0, V2) or QR (mode 1, U2) chain of p x k windows; reflector vectors
+// to wy + i*stride (ld = window height), coefficients to wy + i*stride + stride/2.
+// The reduced k x k triangle (L-hat_1 bottom / R-tilde_1 top) goes to tri.
+__device__ void run_chain(int mode, double* Xg, long ld, int p, int k, double* wy, size_t stride, double* tri,
+                          double* sm) {
+  FSm f = fsm(sm);
   const int nwin = ht_num_windows(p, k);
   for (int i = 0; i < nwin; ++i) {
     int r0, r1;
     if (mode == 0) ht_ql_window(p, k, i, &r0, &r1);
     else ht_qr_window(p, k, i, &r0, &r1);
-    factor_window(X, ld, r0, r1 - r0, k, mode == 0, wy + (size_t)i * stride, stride, sm);
+    const int w = r1 - r0;
+    for (int e = threadIdx.x; e < w * k; e += blockDim.x) {
+      const int r = e % w, c = e / w;
+      f.X[e] = Xg[(size_t)(r0 + r) + (size_t)c * ld];
+    }
+    __syncthreads();
+    house_factor(f.X, w, k, mode == 0, f.Vs, f.tau, f.nrm);
+    double* Vw = wy + (size_t)i * stride;
+    double* tw = Vw + stride / 2;
+    for (int e = threadIdx.x; e < w * k; e += blockDim.x) {
+      const int r = e % w, c = e / w;
+      Xg[(size_t)(r0 + r) + (size_t)c * ld] = f.X[e];
+      Vw[e] = f.Vs[e];
+    }
+    for (int q = threadIdx.x; q < k; q += blockDim.x) tw[q] = f.tau[q];
+    __syncthreads();
   }
-  // triangular factor: QL -> bottom k rows, QR -> top k rows
   const int tr0 = (mode == 0) ? p - k : 0;
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
     const int r = e % k, c = e / k;
-    tri[e] = X[(size_t)(tr0 + r) + (size_t)c * ld];
+    tri[e] = Xg[(size_t)(tr0 + r) + (size_t)c * ld];
   }
 }
 
-// mode 2: RQ of a rows x cols block of B (rows <= cols) in place -> [0 R1]
-// mode 3: QR of a rows x cols block (rows >= cols) in place -> [R; 0]
-__global__ void __launch_bounds__(HT_THREADS) factor_block_kernel(int mode, double* Xg, long ld, int rows, int cols,
-                                                                   double* wy, size_t stride) {
+__global__ void __launch_bounds__(HT_THREADS) chains_kernel(double* V2, double* U2, long ld, int p, int k,
+                                                             double* wyR, double* wyL, size_t stride, double* L1,
+                                                             double* R1) {
   extern __shared__ double sm[];
-  double* X = sm;
-  double* Vs = X + MAXW * HT_NB_MAX;
-  double* Tm = Vs + MAXW * HT_NB_MAX;
-  double* Gm = Tm + HT_NB_MAX * HT_NB_MAX;
-  double* tau = Gm + HT_NB_MAX * HT_NB_MAX;
-  double* red = tau + HT_NB_MAX;
-  // work on the w x kk matrix: QR -> the block itself; RQ -> its transpose
-  const bool rq = (mode == 2);
-  const int w = rq ? cols : rows, kk = rq ? rows : cols;
-  for (int e = threadIdx.x; e < w * kk; e += blockDim.x) {
-    const int r = e % w, c = e / w;
-    X[e] = rq ? Xg[(size_t)c + (size_t)r * ld] : Xg[(size_t)r + (size_t)c * ld];
-  }
+  if (blockIdx.x == 0) run_chain(0, V2, ld, p, k, wyR, stride, L1, sm);
+  else run_chain(1, U2, ld, p, k, wyL, stride, R1, sm);
+}
+
+// T and Ww of one window per CTA (grid: nwr windows of wyR, then nwl of wyL)
+__global__ void __launch_bounds__(HT_THREADS) form_wy_kernel(double* wyR, double* wyL, size_t stride, int p, int k,
+                                                              int nwr, int nwl) {
+  extern __shared__ double sm[];
+  FSm f = fsm(sm);
+  const bool right = (int)blockIdx.x < nwr;
+  const int i = right ? (int)blockIdx.x : (int)blockIdx.x - nwr;
+  if (!right && i >= nwl) return;
+  int r0, r1;
+  if (right) ht_ql_window(p, k, i, &r0, &r1);
+  else ht_qr_window(p, k, i, &r0, &r1);
+  const int w = r1 - r0;
+  double* Vw = (right ? wyR : wyL) + (size_t)i * stride;
+  double* Ww = Vw + stride / 2;
+  for (int e = threadIdx.x; e < w * k; e += blockDim.x) f.Vs[e] = Vw[e];
+  for (int q = threadIdx.x; q < k; q += blockDim.x) f.tau[q] = Ww[q];
   __syncthreads();
-  house_factor(X, w, kk, rq, Vs, tau, red);
-  double* Ww = wy + ht_wy_half(stride);
-  form_wy(Vs, tau, w, kk, Tm, Gm, Ww);
-  for (int e = threadIdx.x; e < w * kk; e += blockDim.x) {
-    const int r = e % w, c = e / w;
-    if (rq) Xg[(size_t)c + (size_t)r * ld] = X[e];
-    else Xg[(size_t)r + (size_t)c * ld] = X[e];
-    wy[e] = Vs[e];
+  form_t(f.Vs, f.tau, w, k, f.Tm, f.Gm, f.scr);
+  form_w(f.Vs, f.Tm, w, k, Ww);
+}
+
+// ---------------------------------------------------------------------------
+// Restore chains (cooperative).  Right (mode 2): for t = 0.., block b =
+// nbr-1-t: RQ of B(block row b, cols of blocks b-1..b) -> [0 R1], then the
+// rows above block row b times G.  Left (mode 3): for t = 0.., QR of B(rows of
+// blocks t..t+1, col block t) -> [R; 0], then G^T times those rows over the
+// columns right of block t.  Block coordinates are relative to j+1.
+// ---------------------------------------------------------------------------
+struct RestoreArgs {
+  int mode, p, k, j, n;
+  double* B;
+  long ldb;
+  double* wy;
+  size_t stride;
+  double* tstore;  // T factor of each step (k x k, ld k) for the appliers
+  unsigned long long* ptime;  // optional timers: [16] factor, [17] T, [18] wait, [19] apply
+};
+
+__device__ __forceinline__ unsigned long long rs_now() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// right: X(lines [l0, l1), o0 .. o0+w) <- X G = X - (X V) T V^T;
+// left:  X(o0 .. o0+w, lines) <- G^T X = X - V T^T (V^T X);
+// stripes of SRR lines distributed over all CTAs except `skip`.
+constexpr int SRR = 8;
+__device__ void apply_vt(bool right, double* X, long ldx, int l0, int l1, int o0, int w, int kr, const double* Vw,
+                         const double* Tg, double* Xs, double* Ps, double* P2, int skip) {
+  const int tid = threadIdx.x;
+  const int nstripes = (l1 - l0 + SRR - 1) / SRR;
+  const int nact = (skip >= 0 && (int)gridDim.x > 1) ? gridDim.x - 1 : gridDim.x;
+  int rank = blockIdx.x;
+  if (skip >= 0 && (int)gridDim.x > 1) {
+    if ((int)blockIdx.x == skip) return;
+    if ((int)blockIdx.x > skip) --rank;
+  }
+  for (int sidx = rank; sidx < nstripes; sidx += nact) {
+    const int sb = l0 + sidx * SRR, lines = min(SRR, l1 - sb);
+    for (int e = tid; e < SRR * w; e += blockDim.x) {
+      const int li = right ? e % SRR : e / w, c = right ? e / SRR : e % w;
+      double v = 0.0;
+      if (li < lines)
+        v = right ? X[(size_t)(sb + li) + (size_t)(o0 + c) * ldx] : X[(size_t)(o0 + c) + (size_t)(sb + li) * ldx];
+      Xs[li * MAXW + c] = v;
+    }
+    __syncthreads();
+    for (int e = tid; e < SRR * kr; e += blockDim.x) {
+      const int li = e % SRR, q = e / SRR;
+      double s0 = 0.0, s1 = 0.0;
+      int c = 0;
+      for (; c + 1 < w; c += 2) {
+        s0 += Xs[li * MAXW + c] * __ldcg(Vw + c + (size_t)q * w);
+        s1 += Xs[li * MAXW + c + 1] * __ldcg(Vw + c + 1 + (size_t)q * w);
+      }
+      if (c < w) s0 += Xs[li * MAXW + c] * __ldcg(Vw + c + (size_t)q * w);
+      Ps[li * HT_NB_MAX + q] = s0 + s1;
+    }
+    __syncthreads();
+    // P2(li, :) = P(li, :) T: right (X V) T; left (T^T (V^T X))^T has the same rows
+    for (int e = tid; e < SRR * kr; e += blockDim.x) {
+      const int li = e % SRR, q = e / SRR;
+      double s0 = 0.0;
+      for (int l = 0; l <= q; ++l) s0 += Ps[li * HT_NB_MAX + l] * __ldcg(Tg + l + (size_t)q * kr);
+      P2[li * HT_NB_MAX + q] = s0;
+    }
+    __syncthreads();
+    for (int e = tid; e < SRR * w; e += blockDim.x) {
+      const int li = right ? e % SRR : e / w, c = right ? e / SRR : e % w;
+      if (li >= lines) continue;
+      double s0 = Xs[li * MAXW + c];
+      for (int q = 0; q < kr; ++q) s0 -= P2[li * HT_NB_MAX + q] * __ldcg(Vw + c + (size_t)q * w);
+      if (right) X[(size_t)(sb + li) + (size_t)(o0 + c) * ldx] = s0;
+      else X[(size_t)(o0 + c) + (size_t)(sb + li) * ldx] = s0;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(HT_THREADS, 1) restore_kernel(RestoreArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ double sm[];
+  FSm f = fsm(sm);
+  double* Xs = f.Tm;  // stripe buffers reuse Tm, Gm, scr
+  double* Ps = Xs + SRR * MAXW;
+  double* P2 = Ps + SRR * HT_NB_MAX;
+  const int p = a.p, k = a.k, j1 = a.j + 1;
+  const bool right = (a.mode == 2);
+  const int nsteps = right ? ht_num_right_blocks(p, k) - 1 : ht_num_left_blocks(p, k);
+  const int wcta = (gridDim.x > 1) ? 1 : 0;  // forms Ww of the previous step while the others apply
+  for (int t = 0; t < nsteps; ++t) {
+    int off, width, kr, lim;
+    if (right) {
+      const int bb = ht_num_right_blocks(p, k) - 1 - t;
+      int c0, c1, d0, d1;
+      ht_right_block(p, k, bb - 1, &c0, &c1);
+      ht_right_block(p, k, bb, &d0, &d1);
+      off = c0; width = d1 - c0; kr = d1 - d0; lim = d0;
+    } else {
+      const int nlb = ht_num_left_blocks(p, k);
+      int r0, r1, e0, e1;
+      ht_left_block(p, k, t, &r0, &r1);
+      if (t + 1 < nlb) ht_left_block(p, k, t + 1, &e0, &e1); else e1 = r1;
+      off = r0; width = e1 - r0; kr = r1 - r0; lim = r1;
+    }
+    double* Vw = a.wy + (size_t)t * a.stride;
+    double* Ww = Vw + a.stride / 2;
+    double* Tg = a.tstore + (size_t)t * k * k;  // kr x kr, ld kr
+    if (blockIdx.x == 0) {
+      // right: QL of the transposed block row; left: QR of the block column
+      double* blk = right ? a.B + (size_t)(j1 + lim) + (size_t)(j1 + off) * a.ldb
+                          : a.B + (size_t)(j1 + off) + (size_t)(j1 + off) * a.ldb;
+      const int w = width;
+      for (int e = threadIdx.x; e < w * kr; e += blockDim.x) {
+        const int r = e % w, c = e / w;
+        f.X[e] = right ? blk[(size_t)c + (size_t)r * a.ldb] : blk[(size_t)r + (size_t)c * a.ldb];
+      }
+      __syncthreads();
+      unsigned long long t0 = (a.ptime && threadIdx.x == 0) ? rs_now() : 0ull;
+      house_factor(f.X, w, kr, right, f.Vs, f.tau, f.nrm);
+      unsigned long long t1 = (a.ptime && threadIdx.x == 0) ? rs_now() : 0ull;
+      form_t(f.Vs, f.tau, w, kr, f.Tm, f.Gm, f.scr);
+      if (a.ptime && threadIdx.x == 0) {
+        const unsigned long long t2 = rs_now();
+        a.ptime[16] += t1 - t0;
+        a.ptime[17] += t2 - t1;
+      }
+      for (int e = threadIdx.x; e < w * kr; e += blockDim.x) {
+        const int r = e % w, c = e / w;
+        if (right) blk[(size_t)c + (size_t)r * a.ldb] = f.X[e];
+        else blk[(size_t)r + (size_t)c * a.ldb] = f.X[e];
+        Vw[e] = f.Vs[e];
+      }
+      for (int e = threadIdx.x; e < kr * kr; e += blockDim.x) Tg[e] = f.Tm[e];
+      __threadfence();
+    }
+    unsigned long long tw0 = (a.ptime && blockIdx.x == 0 && threadIdx.x == 0) ? rs_now() : 0ull;
+    grid.sync();
+    if (a.ptime && blockIdx.x == 0 && threadIdx.x == 0) a.ptime[18] += rs_now() - tw0;
+    tw0 = (a.ptime && blockIdx.x == 0 && threadIdx.x == 0) ? rs_now() : 0ull;
+    if ((int)blockIdx.x == wcta && wcta != 0) {
+      // Ww = Vw T^T for the bulk sweeps of A, Z / A, Q (and B's rows above)
+      for (int e = threadIdx.x; e < width * kr; e += blockDim.x) f.Vs[e] = __ldcg(Vw + e);
+      for (int e = threadIdx.x; e < kr * kr; e += blockDim.x) f.Tm[e] = __ldcg(Tg + e);
+      __syncthreads();
+      form_w(f.Vs, f.Tm, width, kr, Ww);
+    } else {
+      if (right) apply_vt(true, a.B, a.ldb, j1, j1 + lim, j1 + off, width, kr, Vw, Tg, Xs, Ps, P2, wcta);
+      else apply_vt(false, a.B, a.ldb, j1 + lim, a.n, j1 + off, width, kr, Vw, Tg, Xs, Ps, P2, wcta);
+    }
+    grid.sync();
+    if (a.ptime && blockIdx.x == 0 && threadIdx.x == 0) a.ptime[19] += rs_now() - tw0;
+  }
+  if (gridDim.x == 1) {
+    // single CTA: form every Ww at the end
+    for (int t = 0; t < nsteps; ++t) {
+      int width, kr;
+      if (right) {
+        const int bb = ht_num_right_blocks(p, k) - 1 - t;
+        int c0, c1, d0, d1;
+        ht_right_block(p, k, bb - 1, &c0, &c1);
+        ht_right_block(p, k, bb, &d0, &d1);
+        width = d1 - c0; kr = d1 - d0;
+      } else {
+        const int nlb = ht_num_left_blocks(p, k);
+        int r0, r1, e0, e1;
+        ht_left_block(p, k, t, &r0, &r1);
+        if (t + 1 < nlb) ht_left_block(p, k, t + 1, &e0, &e1); else e1 = r1;
+        width = e1 - r0; kr = r1 - r0;
+      }
+      double* Vw = a.wy + (size_t)t * a.stride;
+      for (int e = threadIdx.x; e < width * kr; e += blockDim.x) f.Vs[e] = Vw[e];
+      for (int e = threadIdx.x; e < kr * kr; e += blockDim.x) f.Tm[e] = a.tstore[(size_t)t * k * k + e];
+      __syncthreads();
+      form_w(f.Vs, f.Tm, width, kr, Vw + a.stride / 2);
+    }
   }
 }
 
@@ -191,23 +451,34 @@ static int g_factor_attr = 0;
 static void set_factor_attr() {
   if (g_factor_attr) return;
   const int bytes = (int)(factor_smem_doubles() * sizeof(double));
-  cudaFuncSetAttribute(factor_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(factor_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(chains_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(form_wy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(restore_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   g_factor_attr = 1;
 }
 
-cudaError_t ht_launch_factor_chain(cudaStream_t st, int mode, double* X, int ldx, int p, int k, double* wy,
-                                   size_t stride, double* out_tri) {
+cudaError_t ht_launch_chains(cudaStream_t st, double* V2, double* U2, long ld, int p, int k, double* wyR, double* wyL,
+                             size_t stride, double* L1, double* R1) {
   set_factor_attr();
-  factor_chain_kernel<<<1, HT_THREADS, factor_smem_doubles() * sizeof(double), st>>>(mode, X, ldx, p, k, wy, stride,
-                                                                                     out_tri);
+  chains_kernel<<<2, HT_THREADS, factor_smem_doubles() * sizeof(double), st>>>(V2, U2, ld, p, k, wyR, wyL, stride,
+                                                                               L1, R1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int nw = ht_num_windows(p, k);
+  form_wy_kernel<<<2 * nw, HT_THREADS, factor_smem_doubles() * sizeof(double), st>>>(wyR, wyL, stride, p, k, nw, nw);
   return cudaGetLastError();
 }
 
-cudaError_t ht_launch_factor_block(cudaStream_t st, int mode, double* X, int ldx, int rows, int cols, double* wy,
-                                   size_t stride) {
+cudaError_t ht_launch_restore(cudaStream_t st, int mode, int p, int k, int j, int n, double* B, long ldb, double* wy,
+                              size_t stride, double* tstore, unsigned long long* ptime) {
   set_factor_attr();
-  factor_block_kernel<<<1, HT_THREADS, factor_smem_doubles() * sizeof(double), st>>>(mode, X, ldx, rows, cols, wy,
-                                                                                     stride);
-  return cudaGetLastError();
+  const int nsteps = (mode == 2) ? ht_num_right_blocks(p, k) - 1 : ht_num_left_blocks(p, k);
+  if (nsteps <= 0) return cudaSuccess;
+  RestoreArgs a{mode, p, k, j, n, B, ldb, wy, stride, tstore, ptime};
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel((void*)restore_kernel, dim3(sms), dim3(HT_THREADS), args,
+                                     factor_smem_doubles() * sizeof(double), st);
 }

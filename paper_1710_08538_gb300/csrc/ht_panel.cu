@@ -46,20 +46,43 @@ struct PanelArgs {
   PanelStatus* st;
   int* err;
   const double* bnorm;
+  int cap;    // staged rows per CTA (>= ceil(m / G)) when stage != 0
+  int stage;  // 1: U, V, Y rows of the CTA's chunk are kept in shared memory
+  unsigned long long* ptime;  // optional per-phase nanoseconds (CTA 0), 16 slots
+  double* Xinv;    // inverses of the BI x BI diagonal blocks of the trailing B (row-major, per block)
+  int* safe;       // per block: 1 = solve with the inverse, 0 = scaled substitution
+  double* xmax;    // per-CTA partial max |x| of the current block (GS solve)
+  double* wpart;   // chunk partials of the triangular multiply (nchunks x n)
 };
 
+__device__ __forceinline__ unsigned long long ht_now() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // Shared-memory layout (doubles): S, T (nb*nb each), vz, vh (nb+1 each),
-// red (64), tile (BS*BS), red4 (4*BS), acc (BS).
-__host__ __device__ inline size_t smem_doubles(int nb) {
-  return 2 * (size_t)nb * nb + 2 * (size_t)(nb + 1) + 64 + BS * BS + 4 * BS + BS;
+// red (64), tile (BS*BS), red4 (4*BS), acc (BS), rscr (HT_THREADS), and,
+// when `stage` is set, this CTA's rows of U, V and Y (cap x nb each).
+__host__ __device__ inline size_t smem_base_doubles(int nb) {
+  return 2 * (size_t)nb * nb + 2 * (size_t)(nb + 1) + 64 + BS * BS + 4 * BS + BS + HT_THREADS + 32 * HT_TRSV_BI +
+         HT_TRSV_BI;
+}
+__host__ __device__ inline size_t smem_doubles(int nb, int cap) {
+  return smem_base_doubles(nb) + 3 * (size_t)cap * nb;
 }
 
 // out[i] = sum_{r in [rb, re)} M(r, i) * y[r] for i < kk, one partial per CTA.
-__device__ void partial_mty(const double* M, long ld, int kk, const double* y, int rb, int re, double* out) {
+// M is in shared memory when m_shared (indexed M[r + i * ld] as well).
+__device__ void partial_mty(const double* M, long ld, bool m_shared, int kk, const double* y, int rb, int re,
+                            double* out) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int i = wid; i < kk; i += HT_THREADS / 32) {
     double acc = 0.0;
-    for (int r = rb + lane; r < re; r += 32) acc += __ldcg(M + r + (size_t)i * ld) * __ldcg(y + r);
+    for (int r = rb + lane; r < re; r += 32) {
+      const double mv = m_shared ? M[r + (size_t)i * ld] : __ldcg(M + r + (size_t)i * ld);
+      acc += mv * __ldcg(y + r);
+    }
     acc = ht_warp_sum(acc);
     if (lane == 0) out[i] = acc;
   }
@@ -68,11 +91,30 @@ __device__ void partial_mty(const double* M, long ld, int kk, const double* y, i
 // dst[i] = sum over CTAs of part[c * HT_PART_STRIDE + off + i], i < kk.
 // Partials are double-buffered: a phase writes buffer (pc & 1) and the next
 // phase reads it, so no CTA overwrites a slot another CTA is still reading.
-__device__ void reduce_part(const double* part, int off, int kk, double* dst) {
-  for (int i = threadIdx.x; i < kk; i += blockDim.x) {
-    double t = 0.0;
-    for (int c = 0; c < (int)gridDim.x; ++c) t += __ldcg(part + (size_t)c * HT_PART_STRIDE + off + i);
-    dst[i] = t;
+__device__ void reduce_part(const double* part, int off, int kk, double* dst, double* scratch) {
+  // thread t sums CTAs c = t / kk, t / kk + nt, ... of column i = t % kk with
+  // independent loads in flight; the nt partial sums are then added in order.
+  if (kk <= 0) { __syncthreads(); return; }
+  const int nt = max(1, (int)blockDim.x / kk);
+  const int t = threadIdx.x, i = t % kk, g0 = t / kk;
+  if (g0 < nt) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int c = g0;
+    const int G = gridDim.x;
+    for (; c + 3 * nt < G; c += 4 * nt) {
+      s0 += __ldcg(part + (size_t)c * HT_PART_STRIDE + off + i);
+      s1 += __ldcg(part + (size_t)(c + nt) * HT_PART_STRIDE + off + i);
+      s2 += __ldcg(part + (size_t)(c + 2 * nt) * HT_PART_STRIDE + off + i);
+      s3 += __ldcg(part + (size_t)(c + 3 * nt) * HT_PART_STRIDE + off + i);
+    }
+    for (; c < G; c += nt) s0 += __ldcg(part + (size_t)c * HT_PART_STRIDE + off + i);
+    scratch[g0 * kk + i] = (s0 + s1) + (s2 + s3);
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < kk; q += blockDim.x) {
+    double v = 0.0;
+    for (int g = 0; g < nt; ++g) v += scratch[g * kk + q];
+    dst[q] = v;
   }
   __syncthreads();
 }
@@ -84,17 +126,6 @@ __device__ double reduce_scalar(const double* part, int off, double* red, bool i
     t = is_max ? fmax(t, v) : t + v;
   }
   return is_max ? ht_block_max(t, red) : ht_block_sum(t, red);
-}
-
-// Row blocks of the trailing system owned by this CTA, bottom first, in a
-// zigzag over CTAs so that heavy (top) and light (bottom) blocks pair up.
-__device__ __forceinline__ int zz_block(int q, int G, int nblk) {
-  // position q -> block index (bottom first)
-  return nblk - 1 - q;
-}
-__device__ __forceinline__ int zz_owner(int q, int G) {
-  int round = q / G, pos = q % G;
-  return (round & 1) ? (G - 1 - pos) : pos;
 }
 
 // t[r] = sum_c M(r0 + r, c0 + c) * xv[c] for r < rows, c < cols (tile of at
@@ -119,82 +150,105 @@ __device__ void tile_gemv(const double* M, long ld, int r0, int rows, int c0, in
   __syncthreads();
 }
 
-// Scaled backward substitution B_loc y = 2^{-E} rhs over 64-row blocks.  On
-// return (before the next grid barrier) sol holds the stored block values and
-// exps[b] the block exponents: true solution = sol * 2^{exps[b]}.
-__device__ void trsv_blocks(const PanelArgs& a, int m, const double* rhs, double* sol, unsigned epoch, double* tile,
-                            double* red4, double* acc, double* xl, int* shi) {
-  const int G = gridDim.x, nblk = (m + BS - 1) / BS;
-  const double* Bl = a.B + (size_t)(a.s + 1) + (size_t)(a.s + 1) * a.ldb;
-  const long ldb = a.ldb;
-  for (int q = 0; q < nblk; ++q) {
-    if (zz_owner(q, G) != (int)blockIdx.x) continue;
-    const int i = zz_block(q, G, nblk);
-    const int r0 = i * BS, rows = min(BS, m - r0);
-    // diagonal tile (upper part) and right-hand side
-    for (int e = threadIdx.x; e < BS * BS; e += blockDim.x) {
-      int rr = e % BS, cc = e / BS;
+constexpr int BI = HT_TRSV_BI;  // diagonal block of the grid-synchronous solve
+
+// Inverse of the upper triangular bs x bs diagonal block D = B_loc[r0.., r0..]
+// by blocked backward substitution on the identity (32-row sub-blocks from the
+// bottom; thread t owns column t of X).  X is written row-major (ld bs) and
+// the block is marked safe when X is finite and max|X| max|D| <= 2^26; unsafe
+// blocks are solved by scaled substitution instead.  Dsm: 32 x bs scratch.
+__device__ void invert_block(const double* Bl, long ldb, int r0, int bs, double* X, int* safe, double* Dsm,
+                             double* red) {
+  const int tid = threadIdx.x;
+  const int nsb = (bs + 31) / 32;
+  double dmax = 0.0;
+  for (int sb = nsb - 1; sb >= 0; --sb) {
+    const int R0 = sb * 32, rows = min(32, bs - R0), wcols = bs - R0;
+    __syncthreads();
+    for (int e = tid; e < 32 * wcols; e += blockDim.x) {
+      const int rr = e % 32, cc = e / 32;
       double v = 0.0;
-      if (rr < rows && cc < rows && rr <= cc) v = Bl[(size_t)(r0 + rr) + (size_t)(r0 + cc) * ldb];
-      if (rr == cc && rr >= rows) v = 1.0;
+      if (rr < rows && R0 + rr <= R0 + cc) v = Bl[(size_t)(r0 + R0 + rr) + (size_t)(r0 + R0 + cc) * ldb];
+      Dsm[rr + cc * 32] = v;
+      dmax = fmax(dmax, fabs(v));
+    }
+    __syncthreads();
+    for (int t = tid; t < bs; t += blockDim.x) {
+      if (t < R0) {
+        for (int rr = 0; rr < rows; ++rr) X[(size_t)(R0 + rr) * bs + t] = 0.0;
+        continue;
+      }
+      double acc[32];
+#pragma unroll
+      for (int rr = 0; rr < 32; ++rr) acc[rr] = (R0 + rr == t) ? 1.0 : 0.0;
+      for (int c = R0 + rows; c <= t; ++c) {
+        const double xv = X[(size_t)c * bs + t];
+#pragma unroll
+        for (int rr = 0; rr < 32; ++rr) acc[rr] -= Dsm[rr + (c - R0) * 32] * xv;
+      }
+#pragma unroll
+      for (int rr = 31; rr >= 0; --rr) {
+        if (rr >= rows) continue;
+        const double d = Dsm[rr + rr * 32];
+        const double xv = (R0 + rr <= t) ? acc[rr] / d : 0.0;
+        X[(size_t)(R0 + rr) * bs + t] = xv;
+#pragma unroll
+        for (int q = 0; q < 32; ++q)
+          if (q < rr) acc[q] -= Dsm[q + rr * 32] * xv;
+      }
+    }
+  }
+  __syncthreads();
+  double xm = 0.0;
+  bool fin = true;
+  for (int e = tid; e < bs * bs; e += blockDim.x) {
+    const double v = X[e];
+    if (!isfinite(v)) fin = false;
+    xm = fmax(xm, fabs(v));
+  }
+  xm = ht_block_max(fin ? xm : INFINITY, red);
+  dmax = ht_block_max(dmax, red);
+  if (tid == 0) *safe = (isfinite(xm) && xm * dmax <= 67108864.0) ? 1 : 0;
+}
+
+// Scaled substitution of one diagonal block (rows <= BI) by one CTA: acc
+// (shared, rows entries, in the frame of the solve) is overwritten by the
+// solution; returns (in *shift) the exponent added to the block frame so that
+// no |x| exceeds 2^500.  tile: BS x BS scratch, red4: 4*BS scratch.
+__device__ void subst_block(const double* Bl, long ldb, const double* invd, int r0, int rows, double* acc,
+                            double* tile, double* red4, double* xl, int* shi, int* shift) {
+  const int tid = threadIdx.x;
+  if (tid == 0) shi[0] = 0;
+  const int nsub = (rows + BS - 1) / BS;
+  for (int sbk = nsub - 1; sbk >= 0; --sbk) {
+    const int q0 = sbk * BS, qr = min(BS, rows - q0);
+    __syncthreads();
+    for (int e = tid; e < BS * BS; e += blockDim.x) {
+      const int rr = e % BS, cc = e / BS;
+      double v = 0.0;
+      if (rr < qr && cc < qr && rr <= cc) v = Bl[(size_t)(r0 + q0 + rr) + (size_t)(r0 + q0 + cc) * ldb];
+      if (rr == cc && rr >= qr) v = 1.0;
       tile[e] = v;
     }
-    if (threadIdx.x < BS) acc[threadIdx.x] = (threadIdx.x < rows) ? __ldcg(rhs + r0 + threadIdx.x) : 0.0;
-    if (threadIdx.x == 0) shi[0] = 0;  // block exponent E
     __syncthreads();
-    for (int l = nblk - 1; l > i; --l) {
-      if (threadIdx.x == 0) {
-        int spins = 0;
-        while (ht_ld_acquire(a.flags + l) != (int)epoch) {
-          if (++spins > HT_SPIN_LIMIT || ht_ld_acquire(a.err) != 0) {
-            atomicCAS(a.err, 0, HT_ERR_TIMEOUT);
-            break;
-          }
-          __nanosleep(32);
-        }
-        shi[1] = __ldcg(a.exps + l);
-      }
-      __syncthreads();
-      const int c0 = l * BS, cols = min(BS, m - c0);
-      if (threadIdx.x < BS) xl[threadIdx.x] = (threadIdx.x < cols) ? __ldcg(sol + c0 + threadIdx.x) : 0.0;
-      __syncthreads();
-      tile_gemv(Bl, ldb, r0, rows, c0, cols, xl, red4, red4 + 0);  // result in red4[0..BS)
-      // red4[0..BS) now holds the tile product (tile_gemv wrote out == red4)
-      const int el = shi[1];
-      if (threadIdx.x < BS) {
-        int E = shi[0];
-        double av = acc[threadIdx.x];
-        if (el > E) { av = ldexp(av, E - el); E = el; }
-        av -= ldexp(red4[threadIdx.x], el - E);
-        acc[threadIdx.x] = av;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0 && el > shi[0]) shi[0] = el;
-      __syncthreads();
-    }
-    // substitution inside the block by warp 0 (rows lane, lane + 32)
-    if (threadIdx.x < 32) {
-      const int lane = threadIdx.x;
-      double a0 = acc[lane], a1 = acc[lane + 32];
-      int E = shi[0];
+    if (tid < 32) {
+      const int lane = tid;
+      double a0 = (lane < qr) ? acc[q0 + lane] : 0.0, a1 = (lane + 32 < qr) ? acc[q0 + lane + 32] : 0.0;
+      int E = 0;
       for (int c = BS - 1; c >= 0; --c) {
         const double t = __shfl_sync(0xffffffffu, (c >= 32) ? a1 : a0, c & 31);
         const double d = tile[c + c * BS];
         double xc;
-        if (c >= rows) {
+        if (c >= qr) {
           xc = 0.0;
+        } else if (fabs(t) > ldexp(fabs(d), HT_BIG_EXP)) {
+          const int sh = ilogb(t) - ilogb(d) - HT_BIG_EXP + 2;
+          a0 = ldexp(a0, -sh);
+          a1 = ldexp(a1, -sh);
+          E += sh;
+          xc = ldexp(t, -sh) * invd[r0 + q0 + c];
         } else {
-          if (fabs(t) > ldexp(fabs(d), HT_BIG_EXP)) {
-            // rescale the whole block so that |x_c| stays below 2^500
-            int sh = ilogb(t) - ilogb(d) - HT_BIG_EXP + 2;
-            a0 = ldexp(a0, -sh);
-            a1 = ldexp(a1, -sh);
-            E += sh;
-            const double t2 = ldexp(t, -sh);
-            xc = t2 * a.invd[r0 + c];
-          } else {
-            xc = t * a.invd[r0 + c];
-          }
+          xc = t * invd[r0 + q0 + c];
         }
         if (lane == (c & 31)) {
           if (c >= 32) a1 = xc; else a0 = xc;
@@ -202,17 +256,129 @@ __device__ void trsv_blocks(const PanelArgs& a, int m, const double* rhs, double
         if (lane < c) a0 -= tile[lane + c * BS] * xc;
         if (lane + 32 < c) a1 -= tile[lane + 32 + c * BS] * xc;
       }
-      if (lane < rows) sol[r0 + lane] = a0;
-      if (lane + 32 < rows) sol[r0 + lane + 32] = a1;
-      if (lane == 0) a.exps[i] = E;
-      __threadfence();
-      __syncwarp();
-      if (lane == 0) ht_st_release(a.flags + i, (int)epoch);
+      if (lane < qr) acc[q0 + lane] = a0;
+      if (lane + 32 < qr) acc[q0 + lane + 32] = a1;
+      if (lane == 0) shi[1] = E;
     }
     __syncthreads();
+    const int sh = shi[1];
+    if (sh != 0) {
+      // the rest of the block shares the frame: rows outside this sub-block
+      for (int r = tid; r < rows; r += blockDim.x)
+        if (r < q0 || r >= q0 + qr) acc[r] = ldexp(acc[r], -sh);
+      if (tid == 0) shi[0] += sh;
+    }
+    __syncthreads();
+    // update the rows above the sub-block: acc[0:q0] -= B[r0.., r0+q0..] x_sub
+    if (q0 > 0) {
+      if (tid < BS) xl[tid] = (tid < qr) ? acc[q0 + tid] : 0.0;
+      __syncthreads();
+      for (int rb = 0; rb < q0; rb += BS) {
+        tile_gemv(Bl, ldb, r0 + rb, min(BS, q0 - rb), r0 + q0, qr, xl, red4, red4);
+        if (tid < min(BS, q0 - rb)) acc[rb + tid] -= red4[tid];
+        __syncthreads();
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0) *shift = shi[0];
+  __syncthreads();
+}
+
+// Grid-synchronous blocked backward substitution B_loc y = 2^{-E} rhs.  For
+// each BI-row diagonal block from the bottom: (S1) x_i from the precomputed
+// inverse, spread over up to 32 CTAs, or by scaled substitution on one CTA;
+// grid barrier; (S2) all CTAs subtract B(0:r0, block) x_i from their rows of
+// the accumulator; grid barrier.  Every CTA tracks the same frame exponent:
+// the stored solution of block i is 2^{-exps[i]} times the true one.
+template <class Grid>
+__device__ void trsv_gs(const PanelArgs& a, Grid& grid, int m, const double* rhs, double* sol, double* accv,
+                        bool force_subst, double* tile, double* red4, double* acc, double* xl, double* xs,
+                        double* red, int* shi) {
+  const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+  const int nbk = (m + BI - 1) / BI;
+  const double* Bl = a.B + (size_t)(a.s + 1) + (size_t)(a.s + 1) * a.ldb;
+  const long ldb = a.ldb;
+  const int NX = min(G, 32);
+  // accumulator = rhs (chunk rows)
+  {
+    const int ch = (m + G - 1) / G, rb = min(m, cta * ch), re = min(m, rb + ch);
+    for (int r = rb + tid; r < re; r += blockDim.x) accv[r] = __ldcg(rhs + r);
+  }
+  int E = 0;
+  grid.sync();
+  for (int i = nbk - 1; i >= 0; --i) {
+    const int r0 = i * BI, rows = min(BI, m - r0);
+    const bool sf = !force_subst && __ldcg(a.safe + i);
+    // ---- S1 ----
+    if (sf) {
+      if (cta < NX) {
+        const int per = (rows + NX - 1) / NX;  // rows of x per CTA
+        const double* Xb = a.Xinv + (size_t)i * BI * BI;
+        double mx = 0.0;
+        for (int rr = cta * per + (tid >> 5); rr < min(rows, (cta + 1) * per); rr += blockDim.x / 32) {
+          const int lane = tid & 31;
+          double t = 0.0;
+          for (int q = rr + lane; q < rows; q += 32) t += __ldcg(Xb + (size_t)rr * rows + q) * __ldcg(accv + r0 + q);
+          t = ht_warp_sum(t);
+          if (lane == 0) sol[r0 + rr] = t;
+          mx = fmax(mx, fabs(t));
+        }
+        mx = ht_block_max(mx, red);
+        if (tid == 0) { a.xmax[cta] = mx; if (cta == 0) a.flags[i] = 0; }
+      }
+    } else if (cta == i % G) {
+      for (int r = tid; r < rows; r += blockDim.x) xs[r] = __ldcg(accv + r0 + r);
+      __syncthreads();
+      int shift = 0;
+      subst_block(Bl, ldb, a.invd, r0, rows, xs, tile, red4, xl, shi, &shift);
+      double mx = 0.0;
+      for (int r = tid; r < rows; r += blockDim.x) { sol[r0 + r] = xs[r]; mx = fmax(mx, fabs(xs[r])); }
+      mx = ht_block_max(mx, red);
+      if (tid == 0) { a.xmax[0] = mx; a.flags[i] = shift; }
+    }
+    grid.sync();
+    // ---- S2 ----
+    double M = 0.0;
+    int delta;
+    {
+      const int nparts = sf ? NX : 1;
+      double t = (tid < nparts) ? __ldcg(a.xmax + tid) : 0.0;
+      M = ht_block_max(t, red);
+      delta = __ldcg(a.flags + i);  // exponent the block added to the frame
+    }
+    const int Ei = E + delta;
+    int En = max(E, Ei);
+    if (M > 0.0 && isfinite(M)) {
+      const int big = ilogb(M) + (Ei - En);
+      if (big > 400) En += big - 300;
+    }
+    const int sh_acc = E - En, sh_x = Ei - En;
+    if (cta == 0 && tid == 0) a.exps[i] = Ei;  // block exponent relative to the start frame
+    if (r0 > 0) {
+      for (int q = tid; q < BI; q += blockDim.x) xs[q] = (q < rows) ? __ldcg(sol + r0 + q) : 0.0;
+      __syncthreads();
+      const int ch = (r0 + G - 1) / G, rb = min(r0, cta * ch), re = min(r0, rb + ch);
+      for (int tb = rb; tb < re; tb += BS) {
+        const int tr = min(BS, re - tb);
+        double sum = 0.0;
+        for (int cc = 0; cc < rows; cc += BS) {
+          tile_gemv(Bl, ldb, tb, tr, r0 + cc, min(BS, rows - cc), xs + cc, red4, red4);
+          if (tid < BS) sum += red4[tid];
+          __syncthreads();
+        }
+        if (tid < tr) {
+          const double av = __ldcg(accv + tb + tid);
+          accv[tb + tid] = ldexp(av, sh_acc) - ldexp(sum, sh_x);
+        }
+      }
+    }
+    E = En;
+    grid.sync();
   }
 }
 
+template <bool STAGE>
 __global__ void __launch_bounds__(HT_THREADS, 1) panel_kernel(PanelArgs a) {
   cg::grid_group grid = cg::this_grid();
   extern __shared__ double sm[];
@@ -225,6 +391,12 @@ __global__ void __launch_bounds__(HT_THREADS, 1) panel_kernel(PanelArgs a) {
   double* tile = red + 64;
   double* red4 = tile + BS * BS;
   double* acc = red4 + 4 * BS;
+  double* rscr = acc + BS;
+  double* Dsm = rscr + HT_THREADS;  // 32 x BI scratch of the block inversion
+  double* xs = Dsm + 32 * BI;       // BI entries: x of the current block
+  double* Us = xs + BI;             // staged rows [rbeg, rend) of U, V, Y (ld cap)
+  double* Vs = Us + (size_t)a.cap * nb;
+  double* Ys = Vs + (size_t)a.cap * nb;
   __shared__ int shi[4];
   __shared__ double xl[BS];
 
@@ -234,32 +406,60 @@ __global__ void __launch_bounds__(HT_THREADS, 1) panel_kernel(PanelArgs a) {
   const int rbeg = min(m, cta * chunk), rend = min(m, rbeg + chunk);
   const double tol = a.tol_scale * 2.0 * kU * (*a.bnorm);
   double* Yl = a.Y + (s + 1);
+  // rows [rbeg, rend) of U, V, Y: shared-memory copies when STAGE (written
+  // through to global memory, which other CTAs and the absorption read)
+  const long lds = STAGE ? (long)a.cap : ldn;
+  const double* Ub = STAGE ? (Us - rbeg) : a.U;
+  const double* Vb = STAGE ? (Vs - rbeg) : a.V;
+  const double* Yb = STAGE ? (Ys - rbeg) : Yl;
+  auto ldr = [&](const double* p) -> double { return STAGE ? *p : __ldcg(p); };
   int pc = 0;  // phase counter selecting the partial-sum buffer
   auto pbuf = [&](int c) { return a.part + (size_t)(c & 1) * G * HT_PART_STRIDE; };
   auto mypart = [&]() { return pbuf(pc) + (size_t)cta * HT_PART_STRIDE; };
 
   for (int e = tid; e < nb * nb; e += blockDim.x) { Ssh[e] = 0.0; Tsh[e] = 0.0; }
   __syncthreads();
+  // inverses of the diagonal blocks of B(s+1:n, s+1:n); B is fixed for the panel
+  {
+    const double* Bl0 = a.B + (size_t)(s + 1) + (size_t)(s + 1) * a.ldb;
+    const int nbk = (m + BI - 1) / BI;
+    for (int b = cta; b < nbk; b += G)
+      invert_block(Bl0, a.ldb, b * BI, min(BI, m - b * BI), a.Xinv + (size_t)b * BI * BI, a.safe + b, Dsm, red);
+  }
+  grid.sync();
 
   unsigned epoch = a.epoch0;
   int k = 0, failed = 0, ir_total = 0, ir_cols = 0;
+  unsigned long long t_last = (a.ptime && cta == 0 && tid == 0) ? ht_now() : 0ull;
+#define PHASE_MARK(id)                                              \
+  do {                                                              \
+    if (a.ptime && cta == 0 && tid == 0) {                          \
+      unsigned long long t_ = ht_now();                             \
+      a.ptime[id] += t_ - t_last;                                   \
+      t_last = t_;                                                  \
+    }                                                               \
+  } while (0)
   for (k = 0; k < a.kmax; ++k) {
     const int j = s + k;
     double* Aj = a.A + (size_t)j * a.lda + (s + 1);  // local rows of column j
     // ---- Phase A: right update of column j, save it, partial U^T a ----
+    for (int i = tid; i < k; i += blockDim.x) vz[i] = __ldcg(a.V + (k - 1) + (size_t)i * ldn);  // V(j, :)
+    __syncthreads();
     for (int r = rbeg + tid; r < rend; r += blockDim.x) {
       double xv = Aj[r];
       a.acol[r] = xv;
       double t = 0.0;
-      for (int i = 0; i < k; ++i) t += __ldcg(Yl + r + (size_t)i * ldn) * __ldcg(a.V + (k - 1) + (size_t)i * ldn);
+#pragma unroll 8
+      for (int i = 0; i < k; ++i) t += ldr(Yb + r + (size_t)i * lds) * vz[i];
       Aj[r] = xv - t;
     }
     __syncthreads();
     ++pc;
-    partial_mty(a.U, ldn, k, Aj, rbeg, rend, mypart());
+    partial_mty(Ub, lds, STAGE, k, Aj, rbeg, rend, mypart());
     grid.sync();
+    PHASE_MARK(0);
     // ---- Phase B: left update (I - U S^T U^T), tail norm ----
-    reduce_part(pbuf(pc), 0, k, vz);
+    reduce_part(pbuf(pc), 0, k, vz, rscr);
     for (int i = tid; i < k; i += blockDim.x) {
       double t = 0.0;
       for (int l = 0; l <= i; ++l) t += Ssh[l + (size_t)i * nb] * vz[l];
@@ -270,7 +470,8 @@ __global__ void __launch_bounds__(HT_THREADS, 1) panel_kernel(PanelArgs a) {
       double tail = 0.0;
       for (int r = rbeg + tid; r < rend; r += blockDim.x) {
         double xv = Aj[r];
-        for (int i = 0; i < k; ++i) xv -= __ldcg(a.U + r + (size_t)i * ldn) * vh[i];
+#pragma unroll 8
+        for (int i = 0; i < k; ++i) xv -= ldr(Ub + r + (size_t)i * lds) * vh[i];
         Aj[r] = xv;
         if (r > k) tail += xv * xv;
       }
@@ -279,6 +480,7 @@ __global__ void __launch_bounds__(HT_THREADS, 1) panel_kernel(PanelArgs a) {
       if (tid == 0) mypart()[0] = tail;
     }
     grid.sync();
+    PHASE_MARK(1);
     // ---- Phase C: left reflector (beta, u) of A(j+1:n, j) ----
     double beta, scal, alpha;
     {
@@ -295,16 +497,18 @@ __global__ void __launch_bounds__(HT_THREADS, 1) panel_kernel(PanelArgs a) {
       for (int r = rbeg + tid; r < rend; r += blockDim.x) {
         double u = (r < k) ? 0.0 : (r == k) ? 1.0 : __ldcg(Aj + r) * scal;
         a.U[r + (size_t)k * ldn] = u;
+        if (STAGE) Us[(r - rbeg) + (size_t)k * lds] = u;
         if (r == k) Aj[r] = alpha;
         else if (r > k) Aj[r] = 0.0;
       }
       __syncthreads();
       ++pc;
-      partial_mty(a.U, ldn, k, a.U + (size_t)k * ldn, rbeg, rend, mypart());
+      partial_mty(Ub, lds, STAGE, k, a.U + (size_t)k * ldn, rbeg, rend, mypart());
     }
     grid.sync();
+    PHASE_MARK(2);
     // ---- Phase D: S growth; first right-hand side c~ = e_k - U (S U(k,:)^T) ----
-    reduce_part(pbuf(pc), 0, k, vz);
+    reduce_part(pbuf(pc), 0, k, vz, rscr);
     for (int i = tid; i < k; i += blockDim.x) {
       double t = 0.0;
       for (int l = i; l < k; ++l) t += Ssh[i + (size_t)l * nb] * vz[l];
@@ -316,7 +520,7 @@ __global__ void __launch_bounds__(HT_THREADS, 1) panel_kernel(PanelArgs a) {
     __syncthreads();
 
     int it = 0, sig_exp = 0;
-    bool first = true, ok = false;
+    bool first = true, ok = false, subst_mode = false;
     double nr2 = 0.0, nx2 = 0.0, xtail2 = 0.0;
     while (true) {
       if (first) {
@@ -331,15 +535,16 @@ __global__ void __launch_bounds__(HT_THREADS, 1) panel_kernel(PanelArgs a) {
         __syncthreads();
         for (int r = rbeg + tid; r < rend; r += blockDim.x) {
           double c = (r == k) ? 1.0 : 0.0;
-          for (int i = 0; i <= k; ++i) c -= __ldcg(a.U + r + (size_t)i * ldn) * vh[i];
+#pragma unroll 8
+          for (int i = 0; i <= k; ++i) c -= ldr(Ub + r + (size_t)i * lds) * vh[i];
           a.ctil[r] = c;
         }
       } else {
         // c~ = (I - U S U^T)[0; res]: partial U^T [0; res]
         ++pc;
-        partial_mty(a.U, ldn, k + 1, a.res, rbeg, rend, mypart());
+        partial_mty(Ub, lds, STAGE, k + 1, a.res, rbeg, rend, mypart());
         grid.sync();
-        reduce_part(pbuf(pc), 0, k + 1, vz);
+        reduce_part(pbuf(pc), 0, k + 1, vz, rscr);
         for (int i = tid; i <= k; i += blockDim.x) {
           double t = 0.0;
           for (int l = i; l <= k; ++l) t += Ssh[i + (size_t)l * nb] * vz[l];
@@ -348,17 +553,20 @@ __global__ void __launch_bounds__(HT_THREADS, 1) panel_kernel(PanelArgs a) {
         __syncthreads();
         for (int r = rbeg + tid; r < rend; r += blockDim.x) {
           double c = __ldcg(a.res + r);
-          for (int i = 0; i <= k; ++i) c -= __ldcg(a.U + r + (size_t)i * ldn) * vh[i];
+#pragma unroll 8
+          for (int i = 0; i <= k; ++i) c -= ldr(Ub + r + (size_t)i * lds) * vh[i];
           a.ctil[r] = c;
         }
       }
       grid.sync();
+      PHASE_MARK(3);
       // ---- Phase E: scaled backward substitution B y~ = 2^-E c~ ----
-      trsv_blocks(a, m, a.ctil, a.ytil, epoch, tile, red4, acc, xl, shi);
+      trsv_gs(a, grid, m, a.ctil, a.ytil, a.w, subst_mode, tile, red4, acc, xl, xs, red, shi);
       ++epoch;
       grid.sync();
+    PHASE_MARK(4);
       // ---- Phase F: common exponent, partial V^T y~ ----
-      const int nblk = (m + BS - 1) / BS;
+      const int nblk = (m + BI - 1) / BI;
       int emax;
       {
         int t = -2147483647;
@@ -376,15 +584,16 @@ __global__ void __launch_bounds__(HT_THREADS, 1) panel_kernel(PanelArgs a) {
         emax = shi[2];
       }
       for (int r = rbeg + tid; r < rend; r += blockDim.x) {
-        const int e = __ldcg(a.exps + r / BS);
+        const int e = __ldcg(a.exps + r / BI);
         a.ytil[r] = ldexp(__ldcg(a.ytil + r), e - emax);
       }
       __syncthreads();
       ++pc;
-      partial_mty(a.V, ldn, k, a.ytil, rbeg, rend, mypart());
+      partial_mty(Vb, lds, STAGE, k, a.ytil, rbeg, rend, mypart());
       grid.sync();
+    PHASE_MARK(5);
       // ---- Phase G: x = [(I - V T^T V^T) y~](k:m), combine with the IR iterate ----
-      reduce_part(pbuf(pc), 0, k, vz);
+      reduce_part(pbuf(pc), 0, k, vz, rscr);
       for (int i = tid; i < k; i += blockDim.x) {
         double t = 0.0;
         for (int l = 0; l <= i; ++l) t += Tsh[l + (size_t)i * nb] * vz[l];
@@ -397,7 +606,8 @@ __global__ void __launch_bounds__(HT_THREADS, 1) panel_kernel(PanelArgs a) {
           double xv = 0.0;
           if (r >= k) {
             double d = __ldcg(a.ytil + r);
-            for (int i = 0; i < k; ++i) d -= __ldcg(a.V + r + (size_t)i * ldn) * vh[i];
+#pragma unroll 8
+            for (int i = 0; i < k; ++i) d -= ldr(Vb + r + (size_t)i * lds) * vh[i];
             xv = first ? d : ldexp(__ldcg(a.x + r), -emax) + d;
             mx = fmax(mx, fabs(xv));
             if (!(fabs(xv) <= 1.79e308)) mx = INFINITY;  // NaN/Inf marker
@@ -410,6 +620,7 @@ __global__ void __launch_bounds__(HT_THREADS, 1) panel_kernel(PanelArgs a) {
       }
       sig_exp = first ? -emax : sig_exp - emax;
       grid.sync();
+    PHASE_MARK(6);
       // ---- Phase H: normalise x to max |x| in [1, 2); partial V^T [0; x] ----
       int sh = 0;
       {
@@ -422,10 +633,11 @@ __global__ void __launch_bounds__(HT_THREADS, 1) panel_kernel(PanelArgs a) {
       sig_exp += sh;
       __syncthreads();
       ++pc;
-      partial_mty(a.V, ldn, k, a.x, rbeg, rend, mypart());
+      partial_mty(Vb, lds, STAGE, k, a.x, rbeg, rend, mypart());
       grid.sync();
+    PHASE_MARK(7);
       // ---- Phase I: w = (I - V T V^T)[0; x] ----
-      reduce_part(pbuf(pc), 0, k, vz);
+      reduce_part(pbuf(pc), 0, k, vz, rscr);
       for (int i = tid; i < k; i += blockDim.x) {
         double t = 0.0;
         for (int l = i; l < k; ++l) t += Tsh[i + (size_t)l * nb] * vz[l];
@@ -434,44 +646,56 @@ __global__ void __launch_bounds__(HT_THREADS, 1) panel_kernel(PanelArgs a) {
       __syncthreads();
       for (int r = rbeg + tid; r < rend; r += blockDim.x) {
         double wv = __ldcg(a.x + r);
-        for (int i = 0; i < k; ++i) wv -= __ldcg(a.V + r + (size_t)i * ldn) * vh[i];
+#pragma unroll 8
+        for (int i = 0; i < k; ++i) wv -= ldr(Vb + r + (size_t)i * lds) * vh[i];
         a.w[r] = wv;
       }
       grid.sync();
-      // ---- Phase J: w2 = B w (row blocks), partial U^T w2 over owned blocks ----
+    PHASE_MARK(8);
+      // ---- Phase J: w2 = B w as chunk partials over the upper staircase ----
+      // items (column chunk ch of CWC columns, row tile rb of BS rows) with
+      // rb * BS < (ch + 1) * CWC, assigned round-robin to CTAs
       {
+        constexpr int CWC = 4 * BS;
         const double* Bl = a.B + (size_t)(s + 1) + (size_t)(s + 1) * a.ldb;
-        double up = 0.0;
-        for (int q = 0; q < nblk; ++q) {
-          if (zz_owner(q, G) != cta) continue;
-          const int i = zz_block(q, G, nblk);
-          const int r0 = i * BS, rows = min(BS, m - r0);
-          double accb = 0.0;
-          for (int c0 = r0; c0 < m; c0 += BS) {
-            const int cols = min(BS, m - c0);
-            if (tid < BS) xl[tid] = (tid < cols) ? __ldcg(a.w + c0 + tid) : 0.0;
+        const int nrb = (m + BS - 1) / BS, nchk = (m + CWC - 1) / CWC;
+        int total = 0;
+        for (int ch = 0; ch < nchk; ++ch) total += min(nrb, 4 * (ch + 1));
+        int ch = 0, base = 0;
+        for (int item = cta; item < total; item += G) {
+          while (item >= base + min(nrb, 4 * (ch + 1))) { base += min(nrb, 4 * (ch + 1)); ++ch; }
+          const int rb = item - base;
+          const int r0 = rb * BS, rows = min(BS, m - r0);
+          double sum = 0.0;
+          for (int cc = ch * CWC; cc < min(m, (ch + 1) * CWC); cc += BS) {
+            const int cols = min(BS, m - cc);
+            if (tid < BS) xl[tid] = (tid < cols) ? __ldcg(a.w + cc + tid) : 0.0;
             __syncthreads();
-            tile_gemv(Bl, a.ldb, r0, rows, c0, cols, xl, red4, red4);
-            if (tid < BS) accb += red4[tid];
+            tile_gemv(Bl, a.ldb, r0, rows, cc, cols, xl, red4, red4);
+            if (tid < BS) sum += red4[tid];
             __syncthreads();
           }
-          if (tid < BS) acc[tid] = accb;
-          if (tid < rows) a.w2[r0 + tid] = accb;
-          __syncthreads();
-          // partial U^T w2 over this block: thread i handles column i
-          for (int c = tid; c <= k; c += blockDim.x) {
-            double t = 0.0;
-            for (int rr = 0; rr < rows; ++rr) t += __ldcg(a.U + r0 + rr + (size_t)c * ldn) * acc[rr];
-            if (c == tid) up += t;
-          }
-          __syncthreads();
+          if (tid < rows) a.wpart[(size_t)ch * n + r0 + tid] = sum;
         }
+      }
+      grid.sync();
+      PHASE_MARK(9);
+      // ---- Phase K1: w2 rows of this CTA, partial U^T w2 ----
+      {
+        constexpr int CWC = 4 * BS;
+        const int nchk = (m + CWC - 1) / CWC;
+        for (int r = rbeg + tid; r < rend; r += blockDim.x) {
+          double v = 0.0;
+          for (int ch = r / CWC; ch < nchk; ++ch) v += __ldcg(a.wpart + (size_t)ch * n + r);
+          a.w2[r] = v;
+        }
+        __syncthreads();
         ++pc;
-        for (int c = tid; c <= k; c += blockDim.x) mypart()[c] = up;
+        partial_mty(Ub, lds, STAGE, k + 1, a.w2, rbeg, rend, mypart());
       }
       grid.sync();
       // ---- Phase K: w3 = (I - U S^T U^T) w2, residual, norms ----
-      reduce_part(pbuf(pc), 0, k + 1, vz);
+      reduce_part(pbuf(pc), 0, k + 1, vz, rscr);
       for (int i = tid; i <= k; i += blockDim.x) {
         double t = 0.0;
         for (int l = 0; l <= i; ++l) t += Ssh[l + (size_t)i * nb] * vz[l];
@@ -484,7 +708,8 @@ __global__ void __launch_bounds__(HT_THREADS, 1) panel_kernel(PanelArgs a) {
         for (int r = rbeg + tid; r < rend; r += blockDim.x) {
           if (r < k) continue;
           double w3 = __ldcg(a.w2 + r);
-          for (int i = 0; i <= k; ++i) w3 -= __ldcg(a.U + r + (size_t)i * ldn) * vh[i];
+#pragma unroll 8
+          for (int i = 0; i <= k; ++i) w3 -= ldr(Ub + r + (size_t)i * lds) * vh[i];
           const double rv = ((r == k) ? sigma : 0.0) - w3;
           a.res[r] = rv;
           const double xv = __ldcg(a.x + r);
@@ -500,11 +725,20 @@ __global__ void __launch_bounds__(HT_THREADS, 1) panel_kernel(PanelArgs a) {
         if (tid == 0) { mypart()[0] = pr; mypart()[1] = px; mypart()[2] = pt; }
       }
       grid.sync();
+    PHASE_MARK(10);
       // ---- Phase L: iterative-refinement decision (identical in every CTA) ----
       nr2 = reduce_scalar(pbuf(pc), 0, red, false);
       nx2 = reduce_scalar(pbuf(pc), 1, red, false);
       xtail2 = reduce_scalar(pbuf(pc), 2, red, false);
       ok = isfinite(nr2) && isfinite(nx2) && nx2 > 0.0 && sqrt(nr2) <= tol * sqrt(nx2);
+      if (!ok && it >= a.max_ir && k == 0 && !subst_mode) {
+        // k = 0: the solve with B alone is backward stable by substitution
+        // (Sec. 3.2.2c); redo the column without the block inverses
+        subst_mode = true;
+        it = 0;
+        first = true;
+        continue;
+      }
       if (ok || it >= a.max_ir) break;
       ++it;
       first = false;
@@ -532,13 +766,15 @@ __global__ void __launch_bounds__(HT_THREADS, 1) panel_kernel(PanelArgs a) {
       for (int r = rbeg + tid; r < rend; r += blockDim.x) {
         const double v = (r < k) ? 0.0 : (r == k) ? 1.0 : __ldcg(a.x + r) * vscal;
         a.V[r + (size_t)k * ldn] = v;
+        if (STAGE) Vs[(r - rbeg) + (size_t)k * lds] = v;
         a.z[r] = v;
       }
       __syncthreads();
       ++pc;
-      partial_mty(a.V, ldn, k, a.z, rbeg, rend, mypart());
+      partial_mty(Vb, lds, STAGE, k, a.z, rbeg, rend, mypart());
     }
     grid.sync();
+    PHASE_MARK(12);
     // ---- Phase O: GEMV partials A(s+1:n, j+1:n) v(k:m) ----
     {
       const int p = m - k;  // columns j+1..n-1
@@ -567,9 +803,10 @@ __global__ void __launch_bounds__(HT_THREADS, 1) panel_kernel(PanelArgs a) {
       if (tid == 0) shi[3] = nch;
     }
     grid.sync();
+    PHASE_MARK(13);
     // ---- Phase P: T growth, Y(:, k) = gamma (A v - Y V^T v) on rows s+1..n-1 ----
     {
-      reduce_part(pbuf(pc), 0, k, vz);
+      reduce_part(pbuf(pc), 0, k, vz, rscr);
       for (int i = tid; i < k; i += blockDim.x) {
         double t = 0.0;
         for (int l = i; l < k; ++l) t += Tsh[i + (size_t)l * nb] * vz[l];
@@ -582,14 +819,20 @@ __global__ void __launch_bounds__(HT_THREADS, 1) panel_kernel(PanelArgs a) {
       const int nch = shi[3];
       for (int r = rbeg + tid; r < rend; r += blockDim.x) {
         double av = 0.0;
+#pragma unroll 4
         for (int c = 0; c < nch; ++c) av += __ldcg(a.ypart + (size_t)c * n + r);
         double t = 0.0;
-        for (int i = 0; i < k; ++i) t += __ldcg(Yl + r + (size_t)i * ldn) * vz[i];
-        Yl[r + (size_t)k * ldn] = gamma * (av - t);
+#pragma unroll 8
+        for (int i = 0; i < k; ++i) t += ldr(Yb + r + (size_t)i * lds) * vz[i];
+        const double yv = gamma * (av - t);
+        Yl[r + (size_t)k * ldn] = yv;
+        if (STAGE) Ys[(r - rbeg) + (size_t)k * lds] = yv;
       }
     }
     grid.sync();
+    PHASE_MARK(14);
   }
+#undef PHASE_MARK
   if (cta == 0) {
     for (int e = tid; e < nb * nb; e += blockDim.x) { a.S[e] = Ssh[e]; a.T[e] = Tsh[e]; }
     if (tid == 0) {
@@ -684,6 +927,14 @@ cudaError_t ht_launch_prepare_B(HtWork& w, double* B, int ldb, int s, uint64_t s
 }
 
 static int g_panel_smem_set = 0;
+static const int kPanelSmemMax = 220 * 1024;
+
+static void set_panel_attr() {
+  if (g_panel_smem_set) return;
+  cudaFuncSetAttribute(panel_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPanelSmemMax);
+  cudaFuncSetAttribute(panel_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPanelSmemMax);
+  g_panel_smem_set = 1;
+}
 
 cudaError_t ht_launch_panel(HtWork& w, double* A, int lda, const double* B, int ldb, int s, int kmax,
                             double tol_scale, int max_ir) {
@@ -701,22 +952,25 @@ cudaError_t ht_launch_panel(HtWork& w, double* A, int lda, const double* B, int 
   a.st = w.status; a.err = w.err; a.bnorm = w.bnorm;
   // epochs used: at most kmax * (max_ir + 1) solves
   w.epoch_host += (unsigned)(kmax * (max_ir + 1) + 1);
-  const size_t smem = smem_doubles(w.nb) * sizeof(double);
-  if (!g_panel_smem_set) {
-    cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    g_panel_smem_set = 1;
-  }
+  const int m = w.n - s - 1;
+  a.cap = (m + w.G - 1) / w.G;
+  a.ptime = w.ptime;
+  a.Xinv = w.Xinv; a.safe = w.safe; a.xmax = w.xmax; a.wpart = w.wpart;
+  size_t smem = smem_doubles(w.nb, a.cap) * sizeof(double);
+  a.stage = smem <= (size_t)kPanelSmemMax - 4096;
+  if (!a.stage) smem = smem_base_doubles(w.nb) * sizeof(double);
+  set_panel_attr();
   void* args[] = {&a};
-  return cudaLaunchCooperativeKernel((void*)panel_kernel, dim3(w.G), dim3(HT_THREADS), args, smem, w.stream);
+  if (a.stage)
+    return cudaLaunchCooperativeKernel((void*)panel_kernel<true>, dim3(w.G), dim3(HT_THREADS), args, smem, w.stream);
+  return cudaLaunchCooperativeKernel((void*)panel_kernel<false>, dim3(w.G), dim3(HT_THREADS), args, smem, w.stream);
 }
 
 int ht_panel_max_ctas(int nb) {
-  int dev = 0, sms = 0, per = 0;
+  (void)nb;
+  int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  g_panel_smem_set = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, panel_kernel, HT_THREADS, smem_doubles(nb) * sizeof(double));
-  if (per < 1) per = 1;
-  return sms * 1;  // one CTA per SM: the phases are latency-bound, not occupancy-bound
+  set_panel_attr();
+  return sms;  // one CTA per SM: the phases are latency-bound, not occupancy-bound
 }
