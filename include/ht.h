@@ -46,7 +46,8 @@ enum {
   HT_ERR_TIMEOUT = 1003,         /* a bounded device-side wait gave up */
   HT_ERR_NONFINITE = 1004,       /* A or B holds a NaN or an infinity */
   HT_ERR_NOT_IMPLEMENTED = 1005, /* option combination not available */
-  HT_ERR_INTERNAL = 1006         /* a device-side consistency check failed */
+  HT_ERR_INTERNAL = 1006,        /* a device-side consistency check failed */
+  HT_ERR_TOO_LARGE = 1007        /* n exceeds the static workspace of ht_reduce_noalloc */
 };
 
 /* Precision of the bulk (level-3) updates of the absorption, Sec. 3.3. */
@@ -127,6 +128,28 @@ int ht_reduce_ex(int n, double* A, int lda, double* B, int ldb, double* Q, int l
  */
 int ht_reduce_batched(int batch, const int* n, double* const* A, const int* lda, double* const* B,
                       const int* ldb, double* const* Q, double* const* Z, int want_qz, ht_stream_t stream);
+
+/*
+ * ht_reduce_noalloc -- ht_reduce (with leading dimensions for Q and Z) for
+ * pencils of order n <= HT_NOALLOC_NMAX that allocates no memory: its whole
+ * device workspace is a static array of the library (8 MiB per GPU that loads
+ * it, held until the process exits).  The paper has no counterpart; this is a
+ * service for callers that cannot let a library allocate device memory -
+ * applications whose own allocator already holds the GPU's memory, callers
+ * that cannot pay for cudaMalloc / cudaFree (cudaFree synchronises the
+ * device), environments that forbid allocations outside their own allocator.
+ *   Arguments and results are those of ht_reduce (default options).
+ *   n > HT_NOALLOC_NMAX returns HT_ERR_TOO_LARGE before any device work.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   All calls share the array, which keeps the last call's contents (each
+ *   call clears what it uses first); calls are serialised by a process-wide
+ *   lock, and each returns after its work on `stream` has finished, because
+ *   calls that overlapped on the GPU would race on the array.
+ */
+#define HT_NOALLOC_NMAX 512
+int ht_reduce_noalloc(int n, double* A, int lda, double* B, int ldb, double* Q, int ldq, double* Z, int ldz,
+                      int want_qz, ht_stream_t stream);
 
 /* ht_last_device_status -- status word written by the device during the
  * last call on `stream` from this host thread (HT_OK, HT_ERR_TIMEOUT,

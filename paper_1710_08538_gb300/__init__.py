@@ -26,11 +26,13 @@ HT_ERR_TIMEOUT = 1003
 HT_ERR_NONFINITE = 1004
 HT_ERR_NOT_IMPLEMENTED = 1005
 HT_ERR_INTERNAL = 1006
+HT_ERR_TOO_LARGE = 1007
+HT_NOALLOC_NMAX = 512
 HT_PREC_FP64 = 0
 HT_PREC_EMU = 1
 
-EXPORTED = ["ht_reduce", "ht_reduce_ex", "ht_reduce_batched", "ht_last_device_status", "ht_finalize",
-            "ht_status_string", "ht_version"]
+EXPORTED = ["ht_reduce", "ht_reduce_ex", "ht_reduce_batched", "ht_reduce_noalloc", "ht_last_device_status",
+            "ht_finalize", "ht_status_string", "ht_version"]
 
 
 class HtOptions(ctypes.Structure):
@@ -84,6 +86,8 @@ def lib() -> ctypes.CDLL:
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_void_p),
                                         ctypes.POINTER(ctypes.c_void_p), ip, vp]
         L.ht_reduce_batched.restype = ctypes.c_int
+        L.ht_reduce_noalloc.argtypes = [ip, dp, ip, dp, ip, dp, ip, dp, ip, ip, vp]
+        L.ht_reduce_noalloc.restype = ctypes.c_int
         L.ht_last_device_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
         L.ht_last_device_status.restype = ctypes.c_int
         L.ht_finalize.argtypes = []
@@ -160,6 +164,17 @@ def reduce_plain(n: int, A_ptr: int, lda: int, B_ptr: int, ldb: int, Q_ptr: int 
                  want_qz: int, stream_ptr: int) -> int:
     """ht_reduce with raw pointers; returns the status code."""
     return lib().ht_reduce(n, A_ptr, lda, B_ptr, ldb, Q_ptr, Z_ptr, want_qz, stream_ptr)
+
+
+def reduce_noalloc(A, B, Q=None, Z=None, want_qz: bool = True, stream=None):
+    """ht_reduce_noalloc (n <= HT_NOALLOC_NMAX, no device allocation) on torch tensors."""
+    n = A.shape[0]
+    qp = Q.data_ptr() if (want_qz and Q is not None) else None
+    zp = Z.data_ptr() if (want_qz and Z is not None) else None
+    ldq = _ld(Q) if (want_qz and Q is not None) else max(1, n)
+    ldz = _ld(Z) if (want_qz and Z is not None) else max(1, n)
+    _check(lib().ht_reduce_noalloc(n, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), qp, ldq, zp, ldz, int(want_qz),
+                                   _stream_ptr(stream)))
 
 
 def reduce_batched(As, Bs, Qs=None, Zs=None, want_qz: bool = True, stream=None):

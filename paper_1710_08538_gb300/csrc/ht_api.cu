@@ -44,12 +44,16 @@ std::vector<PoolEntry*> g_pool;
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
-int alloc_work(PoolEntry* e, int n, int nb) {
-  HtWork& w = e->w;
+}  // namespace
+
+// Workspace layout for order n, panel width nb and G CTAs in the cooperative
+// panel: returns the bytes needed; when b is not null, carves the pointers of
+// w (and *pt, the profile timers) out of the buffer at b.
+size_t ht_layout_work(HtWork& w, char* b, int n, int nb, int G, unsigned long long** pt) {
   std::memset(&w, 0, sizeof(w));
   w.n = n;
   w.nb = nb;
-  w.G = ht_panel_max_ctas(nb);
+  w.G = G;
   w.ychunks = 4;
   const int nblk = n / HT_TRSV_BS + 2;
   const size_t nn = (size_t)n;
@@ -79,10 +83,7 @@ int alloc_work(PoolEntry* e, int n, int nb) {
   const size_t oXmax = take(256);
   const size_t oTst = take(nn * nb + 4 * (size_t)nb * nb);  // (p/k + 1) T factors of k^2 each
   const size_t oWpart = take((size_t)((n + 4 * HT_TRSV_BS - 1) / (4 * HT_TRSV_BS) + 1) * nn);
-  void* base = nullptr;
-  if (cudaMalloc(&base, total) != cudaSuccess) return HT_ERR_NOMEM;
-  cudaMemset(base, 0, total);
-  char* b = (char*)base;
+  if (!b) return total;
   w.U = (double*)(b + oU); w.V = (double*)(b + oV); w.Y = (double*)(b + oY);
   w.S = (double*)(b + oS); w.T = (double*)(b + oT);
   w.vec = (double*)(b + oVec);
@@ -111,7 +112,20 @@ int alloc_work(PoolEntry* e, int n, int nb) {
   w.xmax = (double*)(b + oXmax);
   w.wpart = (double*)(b + oWpart);
   w.tstore = (double*)(b + oTst);
-  e->pt_dev = (unsigned long long*)(b + oPt);
+  if (pt) *pt = (unsigned long long*)(b + oPt);
+  return total;
+}
+
+namespace {
+
+int alloc_work(PoolEntry* e, int n, int nb) {
+  HtWork& w = e->w;
+  const int G = ht_panel_max_ctas(nb);
+  const size_t total = ht_layout_work(w, nullptr, n, nb, G, nullptr);
+  void* base = nullptr;
+  if (cudaMalloc(&base, total) != cudaSuccess) return HT_ERR_NOMEM;
+  cudaMemset(base, 0, total);
+  ht_layout_work(w, (char*)base, n, nb, G, &e->pt_dev);
   e->base = base;
   if (cudaMallocHost((void**)&e->host_status, sizeof(PanelStatus)) != cudaSuccess) {
     cudaFree(base);
@@ -430,12 +444,25 @@ int reduce_impl(int n, double* A, int lda, double* B, int ldb, double* Q, int ld
   }
   PoolEntry* pe = acquire(n, nb, &rc);
   if (!pe) return rc;
-  HtWork& w = pe->w;
+  const int result = ht_reduce_core(pe->w, pe->host_status, pe->pt_dev, n, A, lda, B, ldb, Q, ldq, Z, ldz, want_qz,
+                                    nb, max_ir, tol_scale, seed, opt && opt->profile, stats, st);
+  release(pe);
+  return result;
+}
+
+}  // namespace
+
+// The reduction of Algorithm 1 on a prepared workspace (n >= 3, arguments
+// checked, Q = Z = I already set when want_qz).  host_status: host memory
+// for the per-panel status read-back; pt_dev: profile timers (or null).
+int ht_reduce_core(HtWork& w, PanelStatus* host_status, unsigned long long* pt_dev, int n, double* A, int lda,
+                   double* B, int ldb, double* Q, int ldq, double* Z, int ldz, int want_qz, int nb, int max_ir,
+                   double tol_scale, uint64_t seed, int profile, ht_stats* stats, cudaStream_t st) {
   w.stream = st;
   Prof prof;
-  prof.on = (opt && opt->profile);
-  w.ptime = prof.on ? pe->pt_dev : nullptr;
-  if (prof.on) cudaMemsetAsync(pe->pt_dev, 0, 32 * sizeof(unsigned long long), st);
+  prof.on = profile && pt_dev;
+  w.ptime = prof.on ? pt_dev : nullptr;
+  if (prof.on) cudaMemsetAsync(pt_dev, 0, 32 * sizeof(unsigned long long), st);
   prof.st = st;
   Ctx c{&w, st, n, A, B, Q, Z, lda, ldb, ldq, ldz, want_qz, 0.0, &prof};
   cudaEvent_t ev[4] = {};
@@ -449,9 +476,9 @@ int reduce_impl(int n, double* A, int lda, double* B, int ldb, double* Q, int ld
         ht_launch_check_finite(st, B, ldb, n, 1, w.err) != cudaSuccess) { result = HT_ERR_CUDA; break; }
     {
       int derr = 0;
-      if (cudaMemcpyAsync(&pe->host_status->error, w.err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      if (cudaMemcpyAsync(&host_status->error, w.err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
           cudaStreamSynchronize(st) != cudaSuccess) { result = HT_ERR_CUDA; break; }
-      derr = pe->host_status->error;
+      derr = host_status->error;
       if (derr != 0) { result = derr; break; }
     }
     if (ht_launch_prepare_B(w, B, ldb, 0, seed, 1) != cudaSuccess) { result = HT_ERR_CUDA; break; }
@@ -470,13 +497,13 @@ int reduce_impl(int n, double* A, int lda, double* B, int ldb, double* Q, int ld
         break;
       }
       if (timing) cudaEventRecord(ev[1], st);
-      if (cudaMemcpyAsync(pe->host_status, w.status, sizeof(PanelStatus), cudaMemcpyDeviceToHost, st) !=
+      if (cudaMemcpyAsync(host_status, w.status, sizeof(PanelStatus), cudaMemcpyDeviceToHost, st) !=
               cudaSuccess ||
           cudaStreamSynchronize(st) != cudaSuccess) {
         result = HT_ERR_CUDA;
         break;
       }
-      const PanelStatus ps = *pe->host_status;
+      const PanelStatus ps = *host_status;
       if (ps.error != 0) { result = ps.error; break; }
       int k = ps.k_done;
       if (k < 1) { result = HT_ERR_INTERNAL; break; }
@@ -529,7 +556,7 @@ int reduce_impl(int n, double* A, int lda, double* B, int ldb, double* Q, int ld
   prof.resolve();
   if (stats && prof.on) {
     unsigned long long pt[24];
-    cudaMemcpy(pt, pe->pt_dev, sizeof(pt), cudaMemcpyDeviceToHost);
+    cudaMemcpy(pt, pt_dev, sizeof(pt), cudaMemcpyDeviceToHost);
     for (int q = 0; q < 24; ++q) stats->panel_phase_ms[q] = pt[q] * 1e-6;
   }
   if (stats) {
@@ -547,11 +574,8 @@ int reduce_impl(int n, double* A, int lda, double* B, int ldb, double* Q, int ld
     cudaMemcpy(&derr, w.err, sizeof(int), cudaMemcpyDeviceToHost);
     t_last_status = derr;
   }
-  release(pe);
   return result;
 }
-
-}  // namespace
 
 extern "C" {
 
@@ -613,6 +637,7 @@ const char* ht_status_string(int status) {
     case HT_ERR_NONFINITE: return "A or B holds a NaN or an infinity";
     case HT_ERR_NOT_IMPLEMENTED: return "option combination not available";
     case HT_ERR_INTERNAL: return "a device-side consistency check failed";
+    case HT_ERR_TOO_LARGE: return "n exceeds the static workspace of ht_reduce_noalloc (n <= 512)";
     default: return status < 0 ? "invalid argument" : "unknown status";
   }
 }

@@ -162,6 +162,11 @@ cudaError_t ht_rankk_right_w(cudaStream_t st, double* X, long ldx, int nrows, in
 cudaError_t ht_rankk_left(cudaStream_t st, double* X, long ldx, int col0, int ncols, int r0, int w1, int k,
                           const double* Ut, int ldu, const double* S, int lds);
 int ht_panel_max_ctas(int nb);
+// workspace layout (bytes when b is null) and the driver of Algorithm 1 on it
+size_t ht_layout_work(HtWork& w, char* b, int n, int nb, int G, unsigned long long** pt);
+int ht_reduce_core(HtWork& w, PanelStatus* host_status, unsigned long long* pt_dev, int n, double* A, int lda,
+                   double* B, int ldb, double* Q, int ldq, double* Z, int ldz, int want_qz, int nb, int max_ir,
+                   double tol_scale, uint64_t seed, int profile, ht_stats* stats, cudaStream_t st);
 cudaError_t ht_launch_rankk_right(cudaStream_t st, double* X, long ldx, int nrows, int c1, int c2, int k,
                                   const double* V1, int ldv1, const double* L1, int ldl1, const double* T, int ldt);
 cudaError_t ht_launch_rankk_left(cudaStream_t st, double* X, long ldx, int ncols, int r0, int k, const double* Ut,
