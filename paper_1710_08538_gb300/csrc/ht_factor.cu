@@ -46,9 +46,11 @@ __device__ __forceinline__ void house_scalars(double x0, double tail, double* sc
 // matrix X (shared, ld w) in place.  On return X holds R (upper triangle in
 // rows 0..kk-1) or L (lower triangle in rows w-kk..w-1) with exact zeros
 // elsewhere, Vs (w x kk) the reflector vectors in product order and tau[q].
-// Two block barriers per reflector; the scalars of the next reflector are
-// computed by the single warp that updates the next column (sc[0..2]).
-__device__ void house_factor(double* X, int w, int kk, bool ql, double* Vs, double* tau, double* sc) {
+// Look-ahead: warp 0 updates only the next column to reduce and prepares its
+// reflector scalars (double-buffered in sc) while warps 1.. update the other
+// columns four at a time with a packed cross-lane reduction.  bv (w entries)
+// holds beta * v.  Two block barriers per reflector.
+__device__ void house_factor(double* X, int w, int kk, bool ql, double* Vs, double* tau, double* sc, double* bv) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   for (int e = tid; e < w * kk; e += blockDim.x) Vs[e] = 0.0;
   if (wid == 0) {
@@ -65,24 +67,45 @@ __device__ void house_factor(double* X, int w, int kk, bool ql, double* Vs, doub
     const int c = ql ? (kk - 1 - q) : q;
     const int t = ql ? (w - kk + c) : c;
     const int lo = ql ? 0 : t, hi = ql ? t + 1 : w;
-    const double beta = sc[0], alpha = sc[1], scal = sc[2];
-    for (int r = lo + tid; r < hi; r += blockDim.x) Vs[r + q * w] = (r == t) ? 1.0 : X[r + c * w] * scal;
+    const double* cur = sc + 4 * (q & 1);
+    double* nxt = sc + 4 * ((q + 1) & 1);
+    const double beta = cur[0], alpha = cur[1], scal = cur[2];
+    for (int r = lo + tid; r < hi; r += blockDim.x) {
+      const double v = (r == t) ? 1.0 : X[r + c * w] * scal;
+      Vs[r + q * w] = v;
+      bv[r] = beta * v;
+    }
     if (tid == 0) tau[q] = beta;
     __syncthreads();
-    // update the columns still to reduce, four per warp at a time with a
-    // packed cross-lane reduction of the four dot products (6 FP64 adds
-    // instead of 20); the warp owning the next column also prepares the
-    // next reflector's scalars
     const int cb = ql ? 0 : c + 1, ce = ql ? c : kk;
-    const int cnext = ql ? c - 1 : c + 1;
-    for (int g0 = cb + 4 * wid; g0 < ce; g0 += 4 * nw) {
-      double d[4] = {0.0, 0.0, 0.0, 0.0};
-      if (beta != 0.0) {
+    const int cnext = (q + 1 < kk) ? (ql ? c - 1 : c + 1) : -1;
+    if (wid == 0) {
+      if (cnext >= 0) {
+        // critical path: update column cnext, then its reflector scalars
+        if (beta != 0.0) {
+          double d = 0.0;
+          for (int r = lo + lane; r < hi; r += 32) d += Vs[r + q * w] * X[r + cnext * w];
+          d = ht_warp_sum(d);
+          for (int r = lo + lane; r < hi; r += 32) X[r + cnext * w] -= d * bv[r];
+        }
+        __syncwarp();
+        const int t2 = ql ? (w - kk + cnext) : cnext;
+        const int lo2 = ql ? 0 : t2, hi2 = ql ? t2 + 1 : w;
+        double sq = 0.0;
+        for (int r = lo2 + lane; r < hi2; r += 32)
+          if (r != t2) sq += X[r + cnext * w] * X[r + cnext * w];
+        sq = ht_warp_sum(sq);
+        __syncwarp();
+        if (lane == 0) house_scalars(X[t2 + cnext * w], sq, nxt);
+      }
+    } else if (beta != 0.0) {
+      for (int g0 = cb + 4 * (wid - 1); g0 < ce; g0 += 4 * (nw - 1)) {
+        double d[4] = {0.0, 0.0, 0.0, 0.0};
         for (int r = lo + lane; r < hi; r += 32) {
           const double vr = Vs[r + q * w];
 #pragma unroll
           for (int i = 0; i < 4; ++i)
-            if (g0 + i < ce) d[i] += vr * X[r + (g0 + i) * w];
+            if (g0 + i < ce && g0 + i != cnext) d[i] += vr * X[r + (g0 + i) * w];
         }
         const bool b16 = lane & 16, b8 = lane & 8;
         double s0 = b16 ? d[2] : d[0], s1 = b16 ? d[3] : d[1];
@@ -90,37 +113,22 @@ __device__ void house_factor(double* X, int w, int kk, bool ql, double* Vs, doub
         const double o1 = __shfl_xor_sync(0xffffffffu, b16 ? d[1] : d[3], 16);
         s0 += o0;
         s1 += o1;
-        double s = b8 ? s1 : s0;
-        s += __shfl_xor_sync(0xffffffffu, b8 ? s0 : s1, 8);
-        s += __shfl_xor_sync(0xffffffffu, s, 4);
-        s += __shfl_xor_sync(0xffffffffu, s, 2);
-        s += __shfl_xor_sync(0xffffffffu, s, 1);
-        // column g0 + i sits in lanes with (b16, b8) = (i >> 1, i & 1)
+        double sv = b8 ? s1 : s0;
+        sv += __shfl_xor_sync(0xffffffffu, b8 ? s0 : s1, 8);
+        sv += __shfl_xor_sync(0xffffffffu, sv, 4);
+        sv += __shfl_xor_sync(0xffffffffu, sv, 2);
+        sv += __shfl_xor_sync(0xffffffffu, sv, 1);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) d[i] = __shfl_sync(0xffffffffu, s, 16 * (i >> 1) + 8 * (i & 1)) * beta;
+        for (int i = 0; i < 4; ++i) d[i] = __shfl_sync(0xffffffffu, sv, 16 * (i >> 1) + 8 * (i & 1));
         for (int r = lo + lane; r < hi; r += 32) {
-          const double vr = Vs[r + q * w];
+          const double br = bv[r];
 #pragma unroll
           for (int i = 0; i < 4; ++i)
-            if (g0 + i < ce) X[r + (g0 + i) * w] -= d[i] * vr;
+            if (g0 + i < ce && g0 + i != cnext) X[r + (g0 + i) * w] -= d[i] * br;
         }
-      }
-      if (cnext >= g0 && cnext < min(ce, g0 + 4)) {
-        const int cc = cnext;
-        const int t2 = ql ? (w - kk + cc) : cc;
-        const int lo2 = ql ? 0 : t2, hi2 = ql ? t2 + 1 : w;
-        __syncwarp();  // rows of column cc were updated by other lanes of this warp
-        double sq = 0.0;
-        for (int r = lo2 + lane; r < hi2; r += 32)
-          if (r != t2) sq += X[r + cc * w] * X[r + cc * w];
-        sq = ht_warp_sum(sq);
-        __syncwarp();
-        if (lane == 0) house_scalars(X[t2 + cc * w], sq, sc + 4);
       }
     }
     for (int r = lo + tid; r < hi; r += blockDim.x) X[r + c * w] = (r == t) ? alpha : 0.0;
-    __syncthreads();
-    if (tid < 3) sc[tid] = sc[4 + tid];
     __syncthreads();
   }
 }
@@ -182,13 +190,13 @@ __device__ void form_w(const double* Vs, const double* Tm, int w, int kk, double
   __syncthreads();
 }
 
-// shared layout: X, Vs (MAXW*HT_NB_MAX each), Tm, Gm, scr (HT_NB_MAX^2 each), tau, sc (32)
+// shared layout: X, Vs (MAXW*HT_NB_MAX each), Tm, Gm, scr (HT_NB_MAX^2 each), tau, sc (32), bv (MAXW)
 __host__ __device__ inline size_t factor_smem_doubles() {
-  return 2 * (size_t)MAXW * HT_NB_MAX + 3 * (size_t)HT_NB_MAX * HT_NB_MAX + HT_NB_MAX + 32;
+  return 2 * (size_t)MAXW * HT_NB_MAX + 3 * (size_t)HT_NB_MAX * HT_NB_MAX + HT_NB_MAX + 32 + MAXW;
 }
 
 struct FSm {
-  double *X, *Vs, *Tm, *Gm, *scr, *tau, *nrm;
+  double *X, *Vs, *Tm, *Gm, *scr, *tau, *nrm, *bv;
 };
 __device__ FSm fsm(double* sm) {
   FSm f;
@@ -199,6 +207,7 @@ __device__ FSm fsm(double* sm) {
   f.scr = f.Gm + HT_NB_MAX * HT_NB_MAX;
   f.tau = f.scr + HT_NB_MAX * HT_NB_MAX;
   f.nrm = f.tau + HT_NB_MAX;
+  f.bv = f.nrm + 32;
   return f;
 }
 
@@ -219,7 +228,7 @@ __device__ void run_chain(int mode, double* Xg, long ld, int p, int k, double* w
       f.X[e] = Xg[(size_t)(r0 + r) + (size_t)c * ld];
     }
     __syncthreads();
-    house_factor(f.X, w, k, mode == 0, f.Vs, f.tau, f.nrm);
+    house_factor(f.X, w, k, mode == 0, f.Vs, f.tau, f.nrm, f.bv);
     double* Vw = wy + (size_t)i * stride;
     double* tw = Vw + stride / 2;
     for (int e = threadIdx.x; e < w * k; e += blockDim.x) {
@@ -385,7 +394,7 @@ __global__ void __launch_bounds__(HT_THREADS, 1) restore_kernel(RestoreArgs a) {
       }
       __syncthreads();
       unsigned long long t0 = (a.ptime && threadIdx.x == 0) ? rs_now() : 0ull;
-      house_factor(f.X, w, kr, right, f.Vs, f.tau, f.nrm);
+      house_factor(f.X, w, kr, right, f.Vs, f.tau, f.nrm, f.bv);
       unsigned long long t1 = (a.ptime && threadIdx.x == 0) ? rs_now() : 0ull;
       form_t(f.Vs, f.tau, w, kr, f.Tm, f.Gm, f.scr);
       if (a.ptime && threadIdx.x == 0) {
