@@ -15,6 +15,7 @@
 // Window geometry is recomputed on the device from (p, k) with the same
 // functions the host uses (ht_common.cuh), so no descriptors are copied.
 #include <algorithm>
+#include <mutex>
 
 #include "ht_common.cuh"
 
@@ -70,9 +71,12 @@ struct SweepArgs {
 };
 
 // Right application: rows [line0 + stripe*SR, ...) of X, X(:, c) <- X(:, c) G.
+// The stripe sits in shared memory column-major (Xs[r + c * SR]) so that the
+// lanes of a warp, which take consecutive rows, hit distinct banks; Vw and Ww
+// entries are warp-uniform (broadcast loads through L1).
 __global__ void __launch_bounds__(HT_THREADS) sweep_right_kernel(SweepArgs a) {
-  __shared__ double Xs[SR * MAXW];        // SR x w, row-major by stripe row
-  __shared__ double Ps[SR * HT_NB_MAX];   // SR x nrefl
+  __shared__ double Xs[SR * MAXW];        // SR x w, ld SR
+  __shared__ double Ps[SR * HT_NB_MAX];   // SR x nrefl, ld SR
   const int tid = threadIdx.x;
   const int row_begin = a.line0 + blockIdx.x * SR;
   const int row_end = min(a.line0 + a.nlines, row_begin + SR);
@@ -88,7 +92,7 @@ __global__ void __launch_bounds__(HT_THREADS) sweep_right_kernel(SweepArgs a) {
     const int c0 = a.origin + off;
     for (int e = tid; e < SR * w; e += blockDim.x) {
       const int r = e % SR, c = e / SR;
-      Xs[r * MAXW + c] = (r < rows) ? a.X[(size_t)(row_begin + r) + (size_t)(c0 + c) * a.ldx] : 0.0;
+      Xs[r + c * SR] = (r < rows) ? a.X[(size_t)(row_begin + r) + (size_t)(c0 + c) * a.ldx] : 0.0;
     }
     __syncthreads();
     // P = Xs Vw (SR x kr)
@@ -98,29 +102,39 @@ __global__ void __launch_bounds__(HT_THREADS) sweep_right_kernel(SweepArgs a) {
       double s0 = 0.0, s1 = 0.0;
       int c = 0;
       for (; c + 1 < w; c += 2) {
-        s0 += Xs[r * MAXW + c] * __ldg(v + c);
-        s1 += Xs[r * MAXW + c + 1] * __ldg(v + c + 1);
+        s0 += Xs[r + c * SR] * __ldg(v + c);
+        s1 += Xs[r + (c + 1) * SR] * __ldg(v + c + 1);
       }
-      if (c < w) s0 += Xs[r * MAXW + c] * __ldg(v + c);
-      Ps[r * HT_NB_MAX + q] = s0 + s1;
+      if (c < w) s0 += Xs[r + c * SR] * __ldg(v + c);
+      Ps[r + q * SR] = s0 + s1;
     }
     __syncthreads();
     // Xs -= P Ww^T, write back
     for (int e = tid; e < SR * w; e += blockDim.x) {
       const int r = e % SR, c = e / SR;
       if (r >= rows) continue;
-      double s0 = Xs[r * MAXW + c];
-      for (int q = 0; q < kr; ++q) s0 -= Ps[r * HT_NB_MAX + q] * __ldg(Ww + (size_t)q * w + c);
-      a.X[(size_t)(row_begin + r) + (size_t)(c0 + c) * a.ldx] = s0;
+      double s0 = Xs[r + c * SR], s1 = 0.0;
+      int q = 0;
+      for (; q + 1 < kr; q += 2) {
+        s0 -= Ps[r + q * SR] * __ldg(Ww + (size_t)q * w + c);
+        s1 -= Ps[r + (q + 1) * SR] * __ldg(Ww + (size_t)(q + 1) * w + c);
+      }
+      if (q < kr) s0 -= Ps[r + q * SR] * __ldg(Ww + (size_t)q * w + c);
+      a.X[(size_t)(row_begin + r) + (size_t)(c0 + c) * a.ldx] = s0 + s1;
     }
     __syncthreads();
   }
 }
 
 // Left application: columns [line0 + stripe*SR, ...) of X, X(rows, c) <- G^T X(rows, c).
+// Dynamic shared memory: Xs (w x SR, ld XLD, odd so that lanes taking
+// consecutive columns hit distinct banks) and Ps (nrefl x SR, Ps[c + q * SR]).
+constexpr int XLD = MAXW + 1;
+constexpr size_t SWEEP_LEFT_SMEM = sizeof(double) * ((size_t)XLD * SR + (size_t)HT_NB_MAX * SR);
 __global__ void __launch_bounds__(HT_THREADS) sweep_left_kernel(SweepArgs a) {
-  __shared__ double Xs[MAXW * SR];        // w x SR, column-major (ld MAXW)
-  __shared__ double Ps[HT_NB_MAX * SR];   // kr x SR
+  extern __shared__ double sl_sm[];
+  double* Xs = sl_sm;
+  double* Ps = sl_sm + XLD * SR;
   const int tid = threadIdx.x;
   const int col_begin = a.line0 + blockIdx.x * SR;
   const int col_end = min(a.line0 + a.nlines, col_begin + SR);
@@ -136,37 +150,43 @@ __global__ void __launch_bounds__(HT_THREADS) sweep_left_kernel(SweepArgs a) {
     const int r0 = a.origin + off;
     for (int e = tid; e < w * SR; e += blockDim.x) {
       const int r = e % w, c = e / w;
-      Xs[r + c * MAXW] = (c < cols) ? a.X[(size_t)(r0 + r) + (size_t)(col_begin + c) * a.ldx] : 0.0;
+      Xs[r + c * XLD] = (c < cols) ? a.X[(size_t)(r0 + r) + (size_t)(col_begin + c) * a.ldx] : 0.0;
     }
     __syncthreads();
-    // P = Vw^T Xs (kr x SR)
+    // P = Vw^T Xs (kr x SR): lanes take columns, Vw entries are warp-uniform
     for (int e = tid; e < kr * SR; e += blockDim.x) {
-      const int q = e % kr, c = e / kr;
+      const int c = e % SR, q = e / SR;
       const double* v = Vw + (size_t)q * w;
       double s0 = 0.0, s1 = 0.0;
       int r = 0;
       for (; r + 1 < w; r += 2) {
-        s0 += __ldg(v + r) * Xs[r + c * MAXW];
-        s1 += __ldg(v + r + 1) * Xs[r + 1 + c * MAXW];
+        s0 += __ldg(v + r) * Xs[r + c * XLD];
+        s1 += __ldg(v + r + 1) * Xs[r + 1 + c * XLD];
       }
-      if (r < w) s0 += __ldg(v + r) * Xs[r + c * MAXW];
-      Ps[q + c * HT_NB_MAX] = s0 + s1;
+      if (r < w) s0 += __ldg(v + r) * Xs[r + c * XLD];
+      Ps[c + q * SR] = s0 + s1;
     }
     __syncthreads();
     // Xs -= Ww P, write back
     for (int e = tid; e < w * SR; e += blockDim.x) {
       const int r = e % w, c = e / w;
       if (c >= cols) continue;
-      double s0 = Xs[r + c * MAXW];
-      for (int q = 0; q < kr; ++q) s0 -= __ldg(Ww + (size_t)q * w + r) * Ps[q + c * HT_NB_MAX];
-      a.X[(size_t)(r0 + r) + (size_t)(col_begin + c) * a.ldx] = s0;
+      double s0 = Xs[r + c * XLD], s1 = 0.0;
+      int q = 0;
+      for (; q + 1 < kr; q += 2) {
+        s0 -= __ldg(Ww + (size_t)q * w + r) * Ps[c + q * SR];
+        s1 -= __ldg(Ww + (size_t)(q + 1) * w + r) * Ps[c + (q + 1) * SR];
+      }
+      if (q < kr) s0 -= __ldg(Ww + (size_t)q * w + r) * Ps[c + q * SR];
+      a.X[(size_t)(r0 + r) + (size_t)(col_begin + c) * a.ldx] = s0 + s1;
     }
     __syncthreads();
   }
 }
 
 // X1 (cols c1..c1+w1) -= W T V1^T, X2 (cols c2..c2+k) -= W T L1^T with
-// W = X1 V1 + X2 L1 (X2 absent when c2 < 0).  Row stripes of SRK rows.
+// W = X1 V1 + X2 L1 (X2 absent when c2 < 0).  Row stripes of SRK rows held
+// column-major in shared memory (consecutive lanes, consecutive rows).
 __global__ void __launch_bounds__(HT_THREADS) rankk_right_kernel(double* X, long ldx, int nrows, int c1, int w1,
                                                                   int c2, int k, const double* V1, int ldv1,
                                                                   const double* L1, int ldl1, const double* Tm,
@@ -180,52 +200,55 @@ __global__ void __launch_bounds__(HT_THREADS) rankk_right_kernel(double* X, long
   if (rows <= 0) return;
   for (int e = tid; e < SRK * w1; e += blockDim.x) {
     const int r = e % SRK, c = e / SRK;
-    X1s[r * MAXW + c] = (r < rows) ? X[(size_t)(rb + r) + (size_t)(c1 + c) * ldx] : 0.0;
+    X1s[r + c * SRK] = (r < rows) ? X[(size_t)(rb + r) + (size_t)(c1 + c) * ldx] : 0.0;
   }
   if (c2 >= 0)
     for (int e = tid; e < SRK * k; e += blockDim.x) {
       const int r = e % SRK, c = e / SRK;
-      X2s[r * HT_NB_MAX + c] = (r < rows) ? X[(size_t)(rb + r) + (size_t)(c2 + c) * ldx] : 0.0;
+      X2s[r + c * SRK] = (r < rows) ? X[(size_t)(rb + r) + (size_t)(c2 + c) * ldx] : 0.0;
     }
   __syncthreads();
   for (int e = tid; e < SRK * k; e += blockDim.x) {
     const int r = e % SRK, q = e / SRK;
     double s0 = 0.0;
-    for (int c = 0; c < w1; ++c) s0 += X1s[r * MAXW + c] * __ldg(V1 + c + (size_t)q * ldv1);
+    for (int c = 0; c < w1; ++c) s0 += X1s[r + c * SRK] * __ldg(V1 + c + (size_t)q * ldv1);
     if (c2 >= 0)
-      for (int c = 0; c < k; ++c) s0 += X2s[r * HT_NB_MAX + c] * __ldg(L1 + c + (size_t)q * ldl1);
-    Ws[r * HT_NB_MAX + q] = s0;
+      for (int c = 0; c < k; ++c) s0 += X2s[r + c * SRK] * __ldg(L1 + c + (size_t)q * ldl1);
+    Ws[r + q * SRK] = s0;
   }
   __syncthreads();
   for (int e = tid; e < SRK * k; e += blockDim.x) {
     const int r = e % SRK, q = e / SRK;
     double s0 = 0.0;
-    for (int l = 0; l < k; ++l) s0 += Ws[r * HT_NB_MAX + l] * __ldg(Tm + l + (size_t)q * ldt);
-    W2s[r * HT_NB_MAX + q] = s0;
+    for (int l = 0; l < k; ++l) s0 += Ws[r + l * SRK] * __ldg(Tm + l + (size_t)q * ldt);
+    W2s[r + q * SRK] = s0;
   }
   __syncthreads();
   for (int e = tid; e < SRK * w1; e += blockDim.x) {
     const int r = e % SRK, c = e / SRK;
     if (r >= rows) continue;
-    double s0 = X1s[r * MAXW + c];
-    for (int q = 0; q < k; ++q) s0 -= W2s[r * HT_NB_MAX + q] * __ldg(V1 + c + (size_t)q * ldv1);
+    double s0 = X1s[r + c * SRK];
+    for (int q = 0; q < k; ++q) s0 -= W2s[r + q * SRK] * __ldg(V1 + c + (size_t)q * ldv1);
     X[(size_t)(rb + r) + (size_t)(c1 + c) * ldx] = s0;
   }
   if (c2 >= 0)
     for (int e = tid; e < SRK * k; e += blockDim.x) {
       const int r = e % SRK, c = e / SRK;
       if (r >= rows) continue;
-      double s0 = X2s[r * HT_NB_MAX + c];
-      for (int q = 0; q < k; ++q) s0 -= W2s[r * HT_NB_MAX + q] * __ldg(L1 + c + (size_t)q * ldl1);
+      double s0 = X2s[r + c * SRK];
+      for (int q = 0; q < k; ++q) s0 -= W2s[r + q * SRK] * __ldg(L1 + c + (size_t)q * ldl1);
       X[(size_t)(rb + r) + (size_t)(c2 + c) * ldx] = s0;
     }
 }
 
 // X(r0:r0+w1, cols) -= Ut (S^T (Ut^T X(r0:r0+w1, cols))), column stripes.
+// Xs has an odd leading dimension so that lanes taking consecutive columns
+// hit distinct banks; P and P2 are stored as P[c + q * SRK].
 __global__ void __launch_bounds__(HT_THREADS) rankk_left_kernel(double* X, long ldx, int col0, int ncols, int r0,
                                                                  int w1, int k, const double* Ut, int ldu,
                                                                  const double* S, int lds) {
-  __shared__ double Xs[MAXW * SRK];
+  constexpr int LD = MAXW + 1;
+  __shared__ double Xs[LD * SRK];
   __shared__ double Ps[HT_NB_MAX * SRK];
   __shared__ double P2[HT_NB_MAX * SRK];
   const int tid = threadIdx.x;
@@ -233,28 +256,28 @@ __global__ void __launch_bounds__(HT_THREADS) rankk_left_kernel(double* X, long 
   if (cols <= 0) return;
   for (int e = tid; e < w1 * SRK; e += blockDim.x) {
     const int r = e % w1, c = e / w1;
-    Xs[r + c * MAXW] = (c < cols) ? X[(size_t)(r0 + r) + (size_t)(cb + c) * ldx] : 0.0;
+    Xs[r + c * LD] = (c < cols) ? X[(size_t)(r0 + r) + (size_t)(cb + c) * ldx] : 0.0;
   }
   __syncthreads();
   for (int e = tid; e < k * SRK; e += blockDim.x) {
-    const int q = e % k, c = e / k;
+    const int c = e % SRK, q = e / SRK;
     double s0 = 0.0;
-    for (int r = 0; r < w1; ++r) s0 += __ldg(Ut + r + (size_t)q * ldu) * Xs[r + c * MAXW];
-    Ps[q + c * HT_NB_MAX] = s0;
+    for (int r = 0; r < w1; ++r) s0 += __ldg(Ut + r + (size_t)q * ldu) * Xs[r + c * LD];
+    Ps[c + q * SRK] = s0;
   }
   __syncthreads();
   for (int e = tid; e < k * SRK; e += blockDim.x) {
-    const int q = e % k, c = e / k;
+    const int c = e % SRK, q = e / SRK;
     double s0 = 0.0;
-    for (int l = 0; l < k; ++l) s0 += __ldg(S + l + (size_t)q * lds) * Ps[l + c * HT_NB_MAX];  // S^T
-    P2[q + c * HT_NB_MAX] = s0;
+    for (int l = 0; l < k; ++l) s0 += __ldg(S + l + (size_t)q * lds) * Ps[c + l * SRK];  // S^T
+    P2[c + q * SRK] = s0;
   }
   __syncthreads();
   for (int e = tid; e < w1 * SRK; e += blockDim.x) {
     const int r = e % w1, c = e / w1;
     if (c >= cols) continue;
-    double s0 = Xs[r + c * MAXW];
-    for (int q = 0; q < k; ++q) s0 -= __ldg(Ut + r + (size_t)q * ldu) * P2[q + c * HT_NB_MAX];
+    double s0 = Xs[r + c * LD];
+    for (int q = 0; q < k; ++q) s0 -= __ldg(Ut + r + (size_t)q * ldu) * P2[c + q * SRK];
     X[(size_t)(r0 + r) + (size_t)(cb + c) * ldx] = s0;
   }
 }
@@ -396,11 +419,31 @@ cudaError_t ht_gemm(cudaStream_t st, char ta, char tb, int M, int N, int K, doub
   return ht_gemm_ws(st, ta, tb, M, N, K, alpha, A, lda, Bm, ldb, beta, C, ldc, nullptr, 0);
 }
 
+// The left sweep takes more than the default 48 KB of dynamic shared memory:
+// raise its limit once per device.
+static cudaError_t sweep_left_attr() {
+  static std::mutex mu;
+  static unsigned long long done = 0;  // bit d: set on device d
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev < 64 && (done >> dev) & 1ull) return cudaSuccess;
+  e = cudaFuncSetAttribute(sweep_left_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_LEFT_SMEM);
+  if (e == cudaSuccess && dev < 64) done |= 1ull << dev;
+  return e;
+}
+
 static cudaError_t launch_sweep(cudaStream_t st, bool right, SweepArgs a) {
   if (a.nlines <= 0 || a.t1 <= a.t0) return cudaSuccess;
   const int grid = (a.nlines + SR - 1) / SR;
-  if (right) sweep_right_kernel<<<grid, HT_THREADS, 0, st>>>(a);
-  else sweep_left_kernel<<<grid, HT_THREADS, 0, st>>>(a);
+  if (right) {
+    sweep_right_kernel<<<grid, HT_THREADS, 0, st>>>(a);
+  } else {
+    const cudaError_t e = sweep_left_attr();
+    if (e != cudaSuccess) return e;
+    sweep_left_kernel<<<grid, HT_THREADS, SWEEP_LEFT_SMEM, st>>>(a);
+  }
   return cudaGetLastError();
 }
 

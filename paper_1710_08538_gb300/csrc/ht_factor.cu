@@ -314,12 +314,16 @@ __device__ void apply_vt(bool right, double* X, long ldx, int l0, int l1, int o0
   }
   for (int sidx = rank; sidx < nstripes; sidx += nact) {
     const int sb = l0 + sidx * SRR, lines = min(SRR, l1 - sb);
+    // stripe in shared memory column-major by line (Xs[li + c * SRR]): the
+    // lanes of a warp take consecutive lines, so shared accesses are free of
+    // bank conflicts; for left applications each group of SRR lanes reads
+    // 32 contiguous bytes of four consecutive rows
     for (int e = tid; e < SRR * w; e += blockDim.x) {
-      const int li = right ? e % SRR : e / w, c = right ? e / SRR : e % w;
+      const int li = e % SRR, c = e / SRR;
       double v = 0.0;
       if (li < lines)
         v = right ? X[(size_t)(sb + li) + (size_t)(o0 + c) * ldx] : X[(size_t)(o0 + c) + (size_t)(sb + li) * ldx];
-      Xs[li * MAXW + c] = v;
+      Xs[li + c * SRR] = v;
     }
     __syncthreads();
     for (int e = tid; e < SRR * kr; e += blockDim.x) {
@@ -327,26 +331,26 @@ __device__ void apply_vt(bool right, double* X, long ldx, int l0, int l1, int o0
       double s0 = 0.0, s1 = 0.0;
       int c = 0;
       for (; c + 1 < w; c += 2) {
-        s0 += Xs[li * MAXW + c] * __ldcg(Vw + c + (size_t)q * w);
-        s1 += Xs[li * MAXW + c + 1] * __ldcg(Vw + c + 1 + (size_t)q * w);
+        s0 += Xs[li + c * SRR] * __ldcg(Vw + c + (size_t)q * w);
+        s1 += Xs[li + (c + 1) * SRR] * __ldcg(Vw + c + 1 + (size_t)q * w);
       }
-      if (c < w) s0 += Xs[li * MAXW + c] * __ldcg(Vw + c + (size_t)q * w);
-      Ps[li * HT_NB_MAX + q] = s0 + s1;
+      if (c < w) s0 += Xs[li + c * SRR] * __ldcg(Vw + c + (size_t)q * w);
+      Ps[li + q * SRR] = s0 + s1;
     }
     __syncthreads();
     // P2(li, :) = P(li, :) T: right (X V) T; left (T^T (V^T X))^T has the same rows
     for (int e = tid; e < SRR * kr; e += blockDim.x) {
       const int li = e % SRR, q = e / SRR;
       double s0 = 0.0;
-      for (int l = 0; l <= q; ++l) s0 += Ps[li * HT_NB_MAX + l] * __ldcg(Tg + l + (size_t)q * kr);
-      P2[li * HT_NB_MAX + q] = s0;
+      for (int l = 0; l <= q; ++l) s0 += Ps[li + l * SRR] * __ldcg(Tg + l + (size_t)q * kr);
+      P2[li + q * SRR] = s0;
     }
     __syncthreads();
     for (int e = tid; e < SRR * w; e += blockDim.x) {
-      const int li = right ? e % SRR : e / w, c = right ? e / SRR : e % w;
+      const int li = e % SRR, c = e / SRR;
       if (li >= lines) continue;
-      double s0 = Xs[li * MAXW + c];
-      for (int q = 0; q < kr; ++q) s0 -= P2[li * HT_NB_MAX + q] * __ldcg(Vw + c + (size_t)q * w);
+      double s0 = Xs[li + c * SRR];
+      for (int q = 0; q < kr; ++q) s0 -= P2[li + q * SRR] * __ldcg(Vw + c + (size_t)q * w);
       if (right) X[(size_t)(sb + li) + (size_t)(o0 + c) * ldx] = s0;
       else X[(size_t)(o0 + c) + (size_t)(sb + li) * ldx] = s0;
     }
