@@ -306,14 +306,15 @@ cudaError_t absorb(Ctx& c, int s, int k) {
                            cudaMemcpyDeviceToDevice, st));
   LAUNCH(HT_CLASS_CHAIN_FACTOR, 2.0 * fl_chain(p, k),
          ht_launch_chains(st, V + k, w.U2w, n, p, k, w.wyR, w.wyL, wst, w.L1, w.R1));
-  // (c)-(e) step 1: B, Z, A columns j+1..n-1 times the chain
-  LAUNCH(HT_CLASS_SWEEP, fl_sweep(0, p, k, nwr, n, j + 1, false),
-         ht_sweep(st, 1, B, ldb, 0, n, j + 1, w.wyR, wst, 0, p, k, 0, nwr, 1, j + 1));
-  if (c.want_qz)
-    LAUNCH(HT_CLASS_SWEEP, fl_sweep(0, p, k, nwr, n, -1, false),
-           ht_sweep(st, 1, Z, ldz, 0, n, j + 1, w.wyR, wst, 0, p, k, 0, nwr, 0, 0));
-  LAUNCH(HT_CLASS_SWEEP, fl_sweep(0, p, k, nwr, n, -1, false),
-         ht_sweep(st, 1, A, lda, 0, n, j + 1, w.wyR, wst, 0, p, k, 0, nwr, 0, 0));
+  // (c)-(e) step 1: A, Z, B columns j+1..n-1 times the chain, one fused launch
+  {
+    const HtSweepJob jobs[3] = {{A, lda, 1, 0, n, j + 1, 0, 0},
+                                {B, ldb, 1, 0, n, j + 1, 1, j + 1},
+                                {Z, ldz, 1, 0, c.want_qz ? n : 0, j + 1, 0, 0}};
+    const double fl = fl_sweep(0, p, k, nwr, n, j + 1, false) +
+                      (c.want_qz ? 2.0 : 1.0) * fl_sweep(0, p, k, nwr, n, -1, false);
+    LAUNCH(HT_CLASS_SWEEP, fl, ht_sweep_multi(st, jobs, 3, w.wyR, wst, 0, p, k, 0, nwr));
+  }
   // (c)/(d) steps 2-4 and (e) step 3
   const double fl_rk = dn * (4.0 * k * k + 6.0 * k * k);
   LAUNCH(HT_CLASS_RANKK, fl_rk, ht_launch_rankk_right(st, B, ldb, n, s + 1, n - k, k, V, n, w.L1, k, w.T, nb));
@@ -335,13 +336,13 @@ cudaError_t absorb(Ctx& c, int s, int k) {
     if (nbr > 1) LAUNCH(HT_CLASS_RESTORE, fl, ht_launch_restore(st, 2, p, k, j, n, B, ldb, w.wyRR, wst, w.tstore, w.ptime));
   }
   if (nbr > 1) {
-    LAUNCH(HT_CLASS_SWEEP, fl_sweep(2, p, k, nbr - 1, j + 1, -1, false),
-           ht_sweep(st, 1, B, ldb, 0, j + 1, j + 1, w.wyRR, wst, 2, p, k, 0, nbr - 1, 0, 0));
-    LAUNCH(HT_CLASS_SWEEP, fl_sweep(2, p, k, nbr - 1, n, -1, false),
-           ht_sweep(st, 1, A, lda, 0, n, j + 1, w.wyRR, wst, 2, p, k, 0, nbr - 1, 0, 0));
-    if (c.want_qz)
-      LAUNCH(HT_CLASS_SWEEP, fl_sweep(2, p, k, nbr - 1, n, -1, false),
-             ht_sweep(st, 1, Z, ldz, 0, n, j + 1, w.wyRR, wst, 2, p, k, 0, nbr - 1, 0, 0));
+    // rows 0..j of B, all rows of A and Z, one fused launch
+    const HtSweepJob jobs[3] = {{A, lda, 1, 0, n, j + 1, 0, 0},
+                                {Z, ldz, 1, 0, c.want_qz ? n : 0, j + 1, 0, 0},
+                                {B, ldb, 1, 0, j + 1, j + 1, 0, 0}};
+    const double fl = fl_sweep(2, p, k, nbr - 1, j + 1, -1, false) +
+                      (c.want_qz ? 2.0 : 1.0) * fl_sweep(2, p, k, nbr - 1, n, -1, false);
+    LAUNCH(HT_CLASS_SWEEP, fl, ht_sweep_multi(st, jobs, 3, w.wyRR, wst, 2, p, k, 0, nbr - 1));
   }
 
   // ---- left reflectors, Sec. 3.3.2 ----
@@ -357,13 +358,15 @@ cudaError_t absorb(Ctx& c, int s, int k) {
   LAUNCH(HT_CLASS_OTHER, 0.0, ht_launch_zero(st, Bsp, ldb, k, k, 1));
   const int nwl = ht_num_windows(p, k);
   // (c) step 3, (e) step 1, (d) step 1
-  LAUNCH(HT_CLASS_SWEEP, fl_sweep(1, p, k, nwl, p, 0, true),
-         ht_sweep(st, 0, B, ldb, j + 1, p, j + 1, w.wyL, wst, 1, p, k, 0, nwl, 1, j + 1));
-  LAUNCH(HT_CLASS_SWEEP, fl_sweep(1, p, k, nwl, n - j, -1, true),
-         ht_sweep(st, 0, A, lda, j, n - j, j + 1, w.wyL, wst, 1, p, k, 0, nwl, 0, 0));
-  if (c.want_qz)
-    LAUNCH(HT_CLASS_SWEEP, fl_sweep(1, p, k, nwl, n, -1, false),
-           ht_sweep(st, 1, Q, ldq, 0, n, j + 1, w.wyL, wst, 1, p, k, 0, nwl, 0, 0));
+  {
+    // columns j.. of A and j+1.. of B from the left, all rows of Q from the right, one fused launch
+    const HtSweepJob jobs[3] = {{A, lda, 0, j, n - j, j + 1, 0, 0},
+                                {Q, ldq, 1, 0, c.want_qz ? n : 0, j + 1, 0, 0},
+                                {B, ldb, 0, j + 1, p, j + 1, 1, j + 1}};
+    const double fl = fl_sweep(1, p, k, nwl, p, 0, true) + fl_sweep(1, p, k, nwl, n - j, -1, true) +
+                      (c.want_qz ? fl_sweep(1, p, k, nwl, n, -1, false) : 0.0);
+    LAUNCH(HT_CLASS_SWEEP, fl, ht_sweep_multi(st, jobs, 3, w.wyL, wst, 1, p, k, 0, nwl));
+  }
   // U~ = [U1; R~1] (2k x k) in tmp3 with ld 2k
   double* Ut = w.tmp3;
   LAUNCH(HT_CLASS_OTHER, 0.0,
@@ -390,11 +393,12 @@ cudaError_t absorb(Ctx& c, int s, int k) {
     }
     LAUNCH(HT_CLASS_RESTORE, fl, ht_launch_restore(st, 3, p, k, j, n, B, ldb, w.wyLR, wst, w.tstore, w.ptime));
   }
-  LAUNCH(HT_CLASS_SWEEP, fl_sweep(3, p, k, nlb, n - j, -1, true),
-         ht_sweep(st, 0, A, lda, j, n - j, j + 1, w.wyLR, wst, 3, p, k, 0, nlb, 0, 0));
-  if (c.want_qz)
-    LAUNCH(HT_CLASS_SWEEP, fl_sweep(3, p, k, nlb, n, -1, false),
-           ht_sweep(st, 1, Q, ldq, 0, n, j + 1, w.wyLR, wst, 3, p, k, 0, nlb, 0, 0));
+  {
+    const HtSweepJob jobs[2] = {{A, lda, 0, j, n - j, j + 1, 0, 0}, {Q, ldq, 1, 0, c.want_qz ? n : 0, j + 1, 0, 0}};
+    const double fl = fl_sweep(3, p, k, nlb, n - j, -1, true) +
+                      (c.want_qz ? fl_sweep(3, p, k, nlb, n, -1, false) : 0.0);
+    LAUNCH(HT_CLASS_SWEEP, fl, ht_sweep_multi(st, jobs, 2, w.wyLR, wst, 3, p, k, 0, nlb));
+  }
   return cudaGetLastError();
 }
 

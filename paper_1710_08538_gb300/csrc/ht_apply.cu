@@ -56,43 +56,54 @@ __device__ __forceinline__ void win_geom(int mode, int p, int k, int t, int* off
   }
 }
 
-struct SweepArgs {
+// One launch applies the same chain to up to HT_SWEEP_MAXJOBS independent
+// targets (B, A, Z or Q of one absorption step), each a "job" with its own
+// direction and line range; the CTAs of job i are [cta0_i, cta0_{i+1}).
+// Fusing the targets fills the GPU even when one target has few stripes.
+struct SweepJob {
   double* X;
   long ldx;
-  int nlines;      // rows (right) or columns (left) of X swept
+  int right;       // 1: X(:, win) <- X(:, win) G;  0: X(win, :) <- G^T X(win, :)
+  int line0;       // first row (right) / column (left) swept
+  int nlines;      // rows (right) or columns (left) swept
   int origin;      // column (right) or row (left) index of window offset 0
-  const double* wy;
-  int mode, p, k, t0, t1;
   int use_limit;   // 1: skip stripes the structural limit says are zero
   int limit_base;  // added to the window limit
-  int line0;       // first row (right) / column (left) of the swept range
-  int ex_off, ex_width, ex_nrefl;  // mode 4
-  long stride;     // doubles between consecutive windows of the WY store (Ww at stride / 2)
+  int cta0;        // first CTA of the job
 };
 
-// Right application: rows [line0 + stripe*SR, ...) of X, X(:, c) <- X(:, c) G.
+struct SweepBatch {
+  SweepJob job[HT_SWEEP_MAXJOBS];
+  int njobs;
+  const double* wy;
+  long stride;     // doubles between consecutive windows of the WY store (Ww at stride / 2)
+  int mode, p, k, t0, t1;
+  int ex_off, ex_width, ex_nrefl;  // mode 4
+};
+
+// Right application to rows [line0 + stripe*SR, ...) of X, X(:, c) <- X(:, c) G.
 // The stripe sits in shared memory column-major (Xs[r + c * SR]) so that the
 // lanes of a warp, which take consecutive rows, hit distinct banks; Vw and Ww
 // entries are warp-uniform (broadcast loads through L1).
-__global__ void __launch_bounds__(HT_THREADS) sweep_right_kernel(SweepArgs a) {
-  __shared__ double Xs[SR * MAXW];        // SR x w, ld SR
-  __shared__ double Ps[SR * HT_NB_MAX];   // SR x nrefl, ld SR
+__device__ void sweep_right_body(const SweepBatch& b, const SweepJob& jb, int stripe, double* Xs, double* Ps) {
   const int tid = threadIdx.x;
-  const int row_begin = a.line0 + blockIdx.x * SR;
-  const int row_end = min(a.line0 + a.nlines, row_begin + SR);
+  const int row_begin = jb.line0 + stripe * SR;
+  const int row_end = min(jb.line0 + jb.nlines, row_begin + SR);
   const int rows = row_end - row_begin;
   if (rows <= 0) return;
-  for (int t = a.t0; t < a.t1; ++t) {
+  double* X = jb.X;
+  const long ldx = jb.ldx;
+  for (int t = b.t0; t < b.t1; ++t) {
     int off, w, kr, lim;
-    if (a.mode == 4) { off = a.ex_off; w = a.ex_width; kr = a.ex_nrefl; lim = 0; }
-    else win_geom(a.mode, a.p, a.k, t, &off, &w, &kr, &lim);
-    if (a.use_limit && row_begin >= a.limit_base + lim) continue;
-    const double* Vw = a.wy + (size_t)t * a.stride;
-    const double* Ww = Vw + a.stride / 2;
-    const int c0 = a.origin + off;
+    if (b.mode == 4) { off = b.ex_off; w = b.ex_width; kr = b.ex_nrefl; lim = 0; }
+    else win_geom(b.mode, b.p, b.k, t, &off, &w, &kr, &lim);
+    if (jb.use_limit && row_begin >= jb.limit_base + lim) continue;
+    const double* Vw = b.wy + (size_t)t * b.stride;
+    const double* Ww = Vw + b.stride / 2;
+    const int c0 = jb.origin + off;
     for (int e = tid; e < SR * w; e += blockDim.x) {
       const int r = e % SR, c = e / SR;
-      Xs[r + c * SR] = (r < rows) ? a.X[(size_t)(row_begin + r) + (size_t)(c0 + c) * a.ldx] : 0.0;
+      Xs[r + c * SR] = (r < rows) ? X[(size_t)(row_begin + r) + (size_t)(c0 + c) * ldx] : 0.0;
     }
     __syncthreads();
     // P = Xs Vw (SR x kr)
@@ -120,37 +131,35 @@ __global__ void __launch_bounds__(HT_THREADS) sweep_right_kernel(SweepArgs a) {
         s1 -= Ps[r + (q + 1) * SR] * __ldg(Ww + (size_t)(q + 1) * w + c);
       }
       if (q < kr) s0 -= Ps[r + q * SR] * __ldg(Ww + (size_t)q * w + c);
-      a.X[(size_t)(row_begin + r) + (size_t)(c0 + c) * a.ldx] = s0 + s1;
+      X[(size_t)(row_begin + r) + (size_t)(c0 + c) * ldx] = s0 + s1;
     }
     __syncthreads();
   }
 }
 
-// Left application: columns [line0 + stripe*SR, ...) of X, X(rows, c) <- G^T X(rows, c).
-// Dynamic shared memory: Xs (w x SR, ld XLD, odd so that lanes taking
-// consecutive columns hit distinct banks) and Ps (nrefl x SR, Ps[c + q * SR]).
+// Left application to columns [line0 + stripe*SR, ...) of X, X(rows, c) <- G^T X(rows, c).
+// Xs is w x SR with the odd leading dimension XLD, so that lanes taking
+// consecutive columns hit distinct banks; Ps is nrefl x SR stored Ps[c + q * SR].
 constexpr int XLD = MAXW + 1;
-constexpr size_t SWEEP_LEFT_SMEM = sizeof(double) * ((size_t)XLD * SR + (size_t)HT_NB_MAX * SR);
-__global__ void __launch_bounds__(HT_THREADS) sweep_left_kernel(SweepArgs a) {
-  extern __shared__ double sl_sm[];
-  double* Xs = sl_sm;
-  double* Ps = sl_sm + XLD * SR;
+__device__ void sweep_left_body(const SweepBatch& b, const SweepJob& jb, int stripe, double* Xs, double* Ps) {
   const int tid = threadIdx.x;
-  const int col_begin = a.line0 + blockIdx.x * SR;
-  const int col_end = min(a.line0 + a.nlines, col_begin + SR);
+  const int col_begin = jb.line0 + stripe * SR;
+  const int col_end = min(jb.line0 + jb.nlines, col_begin + SR);
   const int cols = col_end - col_begin;
   if (cols <= 0) return;
-  for (int t = a.t0; t < a.t1; ++t) {
+  double* X = jb.X;
+  const long ldx = jb.ldx;
+  for (int t = b.t0; t < b.t1; ++t) {
     int off, w, kr, lim;
-    if (a.mode == 4) { off = a.ex_off; w = a.ex_width; kr = a.ex_nrefl; lim = 0; }
-    else win_geom(a.mode, a.p, a.k, t, &off, &w, &kr, &lim);
-    if (a.use_limit && col_end <= a.limit_base + lim) continue;
-    const double* Vw = a.wy + (size_t)t * a.stride;
-    const double* Ww = Vw + a.stride / 2;
-    const int r0 = a.origin + off;
+    if (b.mode == 4) { off = b.ex_off; w = b.ex_width; kr = b.ex_nrefl; lim = 0; }
+    else win_geom(b.mode, b.p, b.k, t, &off, &w, &kr, &lim);
+    if (jb.use_limit && col_end <= jb.limit_base + lim) continue;
+    const double* Vw = b.wy + (size_t)t * b.stride;
+    const double* Ww = Vw + b.stride / 2;
+    const int r0 = jb.origin + off;
     for (int e = tid; e < w * SR; e += blockDim.x) {
       const int r = e % w, c = e / w;
-      Xs[r + c * XLD] = (c < cols) ? a.X[(size_t)(r0 + r) + (size_t)(col_begin + c) * a.ldx] : 0.0;
+      Xs[r + c * XLD] = (c < cols) ? X[(size_t)(r0 + r) + (size_t)(col_begin + c) * ldx] : 0.0;
     }
     __syncthreads();
     // P = Vw^T Xs (kr x SR): lanes take columns, Vw entries are warp-uniform
@@ -178,10 +187,26 @@ __global__ void __launch_bounds__(HT_THREADS) sweep_left_kernel(SweepArgs a) {
         s1 -= __ldg(Ww + (size_t)(q + 1) * w + r) * Ps[c + (q + 1) * SR];
       }
       if (q < kr) s0 -= __ldg(Ww + (size_t)q * w + r) * Ps[c + q * SR];
-      a.X[(size_t)(r0 + r) + (size_t)(col_begin + c) * a.ldx] = s0 + s1;
+      X[(size_t)(r0 + r) + (size_t)(col_begin + c) * ldx] = s0 + s1;
     }
     __syncthreads();
   }
+}
+
+constexpr size_t SWEEP_RIGHT_SMEM = (size_t)SR * MAXW + (size_t)SR * HT_NB_MAX;
+constexpr size_t SWEEP_LEFT_SMEM = (size_t)XLD * SR + (size_t)HT_NB_MAX * SR;
+constexpr size_t SWEEP_SMEM = sizeof(double) * (SWEEP_RIGHT_SMEM > SWEEP_LEFT_SMEM ? SWEEP_RIGHT_SMEM : SWEEP_LEFT_SMEM);
+
+__global__ void __launch_bounds__(HT_THREADS) sweep_kernel(SweepBatch b) {
+  extern __shared__ double sw_sm[];
+  // select the job without indexing the parameter array dynamically
+  SweepJob jb = b.job[0];
+#pragma unroll
+  for (int i = 1; i < HT_SWEEP_MAXJOBS; ++i)
+    if (i < b.njobs && (int)blockIdx.x >= b.job[i].cta0) jb = b.job[i];
+  const int stripe = (int)blockIdx.x - jb.cta0;
+  if (jb.right) sweep_right_body(b, jb, stripe, sw_sm, sw_sm + SR * MAXW);
+  else sweep_left_body(b, jb, stripe, sw_sm, sw_sm + XLD * SR);
 }
 
 // X1 (cols c1..c1+w1) -= W T V1^T, X2 (cols c2..c2+k) -= W T L1^T with
@@ -419,9 +444,9 @@ cudaError_t ht_gemm(cudaStream_t st, char ta, char tb, int M, int N, int K, doub
   return ht_gemm_ws(st, ta, tb, M, N, K, alpha, A, lda, Bm, ldb, beta, C, ldc, nullptr, 0);
 }
 
-// The left sweep takes more than the default 48 KB of dynamic shared memory:
-// raise its limit once per device.
-static cudaError_t sweep_left_attr() {
+// The sweep takes more than the default 48 KB of dynamic shared memory: raise
+// its limit once per device.
+static cudaError_t sweep_attr() {
   static std::mutex mu;
   static unsigned long long done = 0;  // bit d: set on device d
   int dev = 0;
@@ -429,42 +454,52 @@ static cudaError_t sweep_left_attr() {
   if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lk(mu);
   if (dev < 64 && (done >> dev) & 1ull) return cudaSuccess;
-  e = cudaFuncSetAttribute(sweep_left_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_LEFT_SMEM);
+  e = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM);
   if (e == cudaSuccess && dev < 64) done |= 1ull << dev;
   return e;
 }
 
-static cudaError_t launch_sweep(cudaStream_t st, bool right, SweepArgs a) {
-  if (a.nlines <= 0 || a.t1 <= a.t0) return cudaSuccess;
-  const int grid = (a.nlines + SR - 1) / SR;
-  if (right) {
-    sweep_right_kernel<<<grid, HT_THREADS, 0, st>>>(a);
-  } else {
-    const cudaError_t e = sweep_left_attr();
-    if (e != cudaSuccess) return e;
-    sweep_left_kernel<<<grid, HT_THREADS, SWEEP_LEFT_SMEM, st>>>(a);
+static cudaError_t launch_batch(cudaStream_t st, SweepBatch& b, const HtSweepJob* jobs, int njobs) {
+  if (njobs < 1 || njobs > HT_SWEEP_MAXJOBS) return cudaErrorInvalidValue;
+  if (b.t1 <= b.t0) return cudaSuccess;
+  int ctas = 0, nj = 0;
+  for (int i = 0; i < njobs; ++i) {
+    if (jobs[i].nlines <= 0) continue;
+    SweepJob& d = b.job[nj++];
+    d.X = jobs[i].X; d.ldx = jobs[i].ldx; d.right = jobs[i].right; d.line0 = jobs[i].line0;
+    d.nlines = jobs[i].nlines; d.origin = jobs[i].origin; d.use_limit = jobs[i].use_limit;
+    d.limit_base = jobs[i].limit_base; d.cta0 = ctas;
+    ctas += (jobs[i].nlines + SR - 1) / SR;
   }
+  if (nj == 0) return cudaSuccess;
+  b.njobs = nj;
+  const cudaError_t e = sweep_attr();
+  if (e != cudaSuccess) return e;
+  sweep_kernel<<<ctas, HT_THREADS, SWEEP_SMEM, st>>>(b);
   return cudaGetLastError();
+}
+
+cudaError_t ht_sweep_multi(cudaStream_t st, const HtSweepJob* jobs, int njobs, const double* wy, long stride, int mode,
+                           int p, int k, int t0, int t1) {
+  SweepBatch b{};
+  b.wy = wy; b.stride = stride; b.mode = mode; b.p = p; b.k = k; b.t0 = t0; b.t1 = t1;
+  return launch_batch(st, b, jobs, njobs);
 }
 
 cudaError_t ht_sweep(cudaStream_t st, int right, double* X, long ldx, int line0, int nlines, int origin,
                      const double* wy, long stride, int mode, int p, int k, int t0, int t1, int use_limit,
                      int limit_base) {
-  SweepArgs a{};
-  a.X = X; a.ldx = ldx; a.nlines = nlines; a.origin = origin; a.wy = wy; a.stride = stride;
-  a.mode = mode; a.p = p; a.k = k; a.t0 = t0; a.t1 = t1;
-  a.use_limit = use_limit; a.limit_base = limit_base; a.line0 = line0;
-  return launch_sweep(st, right != 0, a);
+  const HtSweepJob j{X, ldx, right, line0, nlines, origin, use_limit, limit_base};
+  return ht_sweep_multi(st, &j, 1, wy, stride, mode, p, k, t0, t1);
 }
 
 cudaError_t ht_apply_single(cudaStream_t st, int right, double* X, long ldx, int line0, int nlines, int origin,
                             int width, int nrefl, const double* wy, long stride) {
-  SweepArgs a{};
-  a.X = X; a.ldx = ldx; a.nlines = nlines; a.origin = origin; a.wy = wy; a.stride = stride;
-  a.mode = 4; a.p = 0; a.k = 0; a.t0 = 0; a.t1 = 1;
-  a.ex_off = 0; a.ex_width = width; a.ex_nrefl = nrefl;
-  a.use_limit = 0; a.limit_base = 0; a.line0 = line0;
-  return launch_sweep(st, right != 0, a);
+  SweepBatch b{};
+  b.wy = wy; b.stride = stride; b.mode = 4; b.t0 = 0; b.t1 = 1;
+  b.ex_off = 0; b.ex_width = width; b.ex_nrefl = nrefl;
+  const HtSweepJob j{X, ldx, right, line0, nlines, origin, 0, 0};
+  return launch_batch(st, b, &j, 1);
 }
 
 cudaError_t ht_launch_rankk_right(cudaStream_t st, double* X, long ldx, int nrows, int c1, int c2, int k,

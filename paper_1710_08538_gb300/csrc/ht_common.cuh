@@ -152,6 +152,20 @@ cudaError_t ht_launch_chains(cudaStream_t st, double* V2, double* U2, long ld, i
 // restore chain of B (mode 2: RQ right, mode 3: QR left), one cooperative launch
 cudaError_t ht_launch_restore(cudaStream_t st, int mode, int p, int k, int j, int n, double* B, long ldb, double* wy,
                               size_t stride, double* tstore, unsigned long long* ptime);
+// One target of a fused chain application (see ht_apply.cu).
+#define HT_SWEEP_MAXJOBS 4
+struct HtSweepJob {
+  double* X;
+  long ldx;
+  int right;       // 1: X(:, win) <- X(:, win) G;  0: X(win, :) <- G^T X(win, :)
+  int line0;       // first row (right) / column (left) swept
+  int nlines;      // rows (right) or columns (left) swept
+  int origin;      // column (right) or row (left) index of window offset 0
+  int use_limit;   // 1: skip stripes that the structural limit says are zero
+  int limit_base;  // added to the window limit
+};
+cudaError_t ht_sweep_multi(cudaStream_t st, const HtSweepJob* jobs, int njobs, const double* wy, long stride, int mode,
+                           int p, int k, int t0, int t1);
 cudaError_t ht_sweep(cudaStream_t st, int right, double* X, long ldx, int line0, int nlines, int origin,
                      const double* wy, long stride, int mode, int p, int k, int t0, int t1, int use_limit,
                      int limit_base);
