@@ -83,6 +83,11 @@ size_t ht_layout_work(HtWork& w, char* b, int n, int nb, int G, unsigned long lo
   const size_t oXmax = take(256);
   const size_t oTst = take(nn * nb + 4 * (size_t)nb * nb);  // (p/k + 1) T factors of k^2 each
   const size_t oWpart = take((size_t)((n + 4 * HT_TRSV_BS - 1) / (4 * HT_TRSV_BS) + 1) * nn);
+  // digits of the emulated sweeps: windows of a chain are processed in launches of emu_cap windows
+  const size_t emu_win = nb <= 32 ? ht_emu_window_bytes(nb) : 0;
+  w.emu_cap = std::min(n / 32 + 4, 1024);
+  const size_t oEmu = take(emu_win ? (emu_win * w.emu_cap + sizeof(double) - 1) / sizeof(double) : 0);
+  const size_t oEmuE = take((size_t)w.emu_cap);
   if (!b) return total;
   w.U = (double*)(b + oU); w.V = (double*)(b + oV); w.Y = (double*)(b + oY);
   w.S = (double*)(b + oS); w.T = (double*)(b + oT);
@@ -110,6 +115,8 @@ size_t ht_layout_work(HtWork& w, char* b, int n, int nb, int G, unsigned long lo
   w.Xinv = (double*)(b + oXinv);
   w.safe = (int*)(b + oSafe);
   w.xmax = (double*)(b + oXmax);
+  w.emu_dig = emu_win ? (void*)(b + oEmu) : nullptr;
+  w.emu_exps = (int*)(b + oEmuE);
   w.wpart = (double*)(b + oWpart);
   w.tstore = (double*)(b + oTst);
   if (pt) *pt = (unsigned long long*)(b + oPt);
@@ -273,6 +280,15 @@ double fl_sweep(int mode, int p, int k, int nwin, double lines, int limit_base, 
   return f;
 }
 
+// One fused chain application, native FP64 or emulated (HT_PREC_EMU).
+cudaError_t run_sweep(Ctx& c, const HtSweepJob* jobs, int njobs, const double* wy, long wst, int mode, int p, int k,
+                      int t0, int t1) {
+  if (c.w->prec == HT_PREC_EMU)
+    return ht_emu_sweep_multi(c.st, jobs, njobs, wy, wst, mode, p, k, t0, t1, c.w->emu_dig, c.w->emu_exps,
+                              c.w->emu_cap);
+  return ht_sweep_multi(c.st, jobs, njobs, wy, wst, mode, p, k, t0, t1);
+}
+
 // Absorption of k right and k left reflectors (Sec. 3.3.1 and 3.3.2).
 cudaError_t absorb(Ctx& c, int s, int k) {
   HtWork& w = *c.w;
@@ -313,7 +329,7 @@ cudaError_t absorb(Ctx& c, int s, int k) {
                                 {Z, ldz, 1, 0, c.want_qz ? n : 0, j + 1, 0, 0}};
     const double fl = fl_sweep(0, p, k, nwr, n, j + 1, false) +
                       (c.want_qz ? 2.0 : 1.0) * fl_sweep(0, p, k, nwr, n, -1, false);
-    LAUNCH(HT_CLASS_SWEEP, fl, ht_sweep_multi(st, jobs, 3, w.wyR, wst, 0, p, k, 0, nwr));
+    LAUNCH(HT_CLASS_SWEEP, fl, run_sweep(c, jobs, 3, w.wyR, wst, 0, p, k, 0, nwr));
   }
   // (c)/(d) steps 2-4 and (e) step 3
   const double fl_rk = dn * (4.0 * k * k + 6.0 * k * k);
@@ -342,7 +358,7 @@ cudaError_t absorb(Ctx& c, int s, int k) {
                                 {B, ldb, 1, 0, j + 1, j + 1, 0, 0}};
     const double fl = fl_sweep(2, p, k, nbr - 1, j + 1, -1, false) +
                       (c.want_qz ? 2.0 : 1.0) * fl_sweep(2, p, k, nbr - 1, n, -1, false);
-    LAUNCH(HT_CLASS_SWEEP, fl, ht_sweep_multi(st, jobs, 3, w.wyRR, wst, 2, p, k, 0, nbr - 1));
+    LAUNCH(HT_CLASS_SWEEP, fl, run_sweep(c, jobs, 3, w.wyRR, wst, 2, p, k, 0, nbr - 1));
   }
 
   // ---- left reflectors, Sec. 3.3.2 ----
@@ -365,7 +381,7 @@ cudaError_t absorb(Ctx& c, int s, int k) {
                                 {B, ldb, 0, j + 1, p, j + 1, 1, j + 1}};
     const double fl = fl_sweep(1, p, k, nwl, p, 0, true) + fl_sweep(1, p, k, nwl, n - j, -1, true) +
                       (c.want_qz ? fl_sweep(1, p, k, nwl, n, -1, false) : 0.0);
-    LAUNCH(HT_CLASS_SWEEP, fl, ht_sweep_multi(st, jobs, 3, w.wyL, wst, 1, p, k, 0, nwl));
+    LAUNCH(HT_CLASS_SWEEP, fl, run_sweep(c, jobs, 3, w.wyL, wst, 1, p, k, 0, nwl));
   }
   // U~ = [U1; R~1] (2k x k) in tmp3 with ld 2k
   double* Ut = w.tmp3;
@@ -397,7 +413,7 @@ cudaError_t absorb(Ctx& c, int s, int k) {
     const HtSweepJob jobs[2] = {{A, lda, 0, j, n - j, j + 1, 0, 0}, {Q, ldq, 1, 0, c.want_qz ? n : 0, j + 1, 0, 0}};
     const double fl = fl_sweep(3, p, k, nlb, n - j, -1, true) +
                       (c.want_qz ? fl_sweep(3, p, k, nlb, n, -1, false) : 0.0);
-    LAUNCH(HT_CLASS_SWEEP, fl, ht_sweep_multi(st, jobs, 2, w.wyLR, wst, 3, p, k, 0, nlb));
+    LAUNCH(HT_CLASS_SWEEP, fl, run_sweep(c, jobs, 2, w.wyLR, wst, 3, p, k, 0, nlb));
   }
   return cudaGetLastError();
 }
@@ -433,7 +449,10 @@ int reduce_impl(int n, double* A, int lda, double* B, int ldb, double* Q, int ld
     seed = opt->seed;
   }
   if (nb > HT_NB_MAX) return HT_ERR_NOT_IMPLEMENTED;
-  if (prec != HT_PREC_FP64) return HT_ERR_NOT_IMPLEMENTED;
+  if (prec != HT_PREC_FP64 && prec != HT_PREC_EMU) return HT_ERR_NOT_IMPLEMENTED;
+  // the emulated sweeps: panels of at most 32 reflectors, 6 digits per operand
+  if (prec == HT_PREC_EMU && (nb > 32 || (opt && opt->emu_slices != 0 && opt->emu_slices != 6)))
+    return HT_ERR_NOT_IMPLEMENTED;
   if (stats) std::memset(stats, 0, sizeof(*stats));
   t_last_status = HT_OK;
   if (n == 0) return HT_OK;
@@ -448,6 +467,7 @@ int reduce_impl(int n, double* A, int lda, double* B, int ldb, double* Q, int ld
   }
   PoolEntry* pe = acquire(n, nb, &rc);
   if (!pe) return rc;
+  pe->w.prec = prec;
   const int result = ht_reduce_core(pe->w, pe->host_status, pe->pt_dev, n, A, lda, B, ldb, Q, ldq, Z, ldz, want_qz,
                                     nb, max_ir, tol_scale, seed, opt && opt->profile, stats, st);
   release(pe);

@@ -129,6 +129,10 @@ struct HtWork {
   double* xmax;            // per-CTA max |x| partials
   double* wpart;           // chunk partials of the triangular multiply
   double* tstore;          // T factors of the restore steps (HT_NB_MAX^2 each)
+  void* emu_dig;           // digits of Vw / Ww for the emulated sweeps (emu_cap windows)
+  int* emu_exps;           // their exponent bounds (2 per window)
+  int emu_cap;             // windows per launch of the emulated sweeps
+  int prec;                // HT_PREC_* of the current call
   cudaStream_t stream;
 };
 #define HT_PART_STRIDE 80   // >= nb + 8 for nb <= 64 ... plus norms
@@ -166,6 +170,11 @@ struct HtSweepJob {
 };
 cudaError_t ht_sweep_multi(cudaStream_t st, const HtSweepJob* jobs, int njobs, const double* wy, long stride, int mode,
                            int p, int k, int t0, int t1);
+// as ht_sweep_multi with FP64 emulated on the tensor cores (ht_emu.cu); needs
+// k <= 32 and a digit buffer of `cap` windows of ht_emu_window_bytes(k) each
+cudaError_t ht_emu_sweep_multi(cudaStream_t st, const HtSweepJob* jobs, int njobs, const double* wy, long stride, int mode,
+                               int p, int k, int t0, int t1, void* dig, int* exps, int cap);
+size_t ht_emu_window_bytes(int nb);
 cudaError_t ht_sweep(cudaStream_t st, int right, double* X, long ldx, int line0, int nlines, int origin,
                      const double* wy, long stride, int mode, int p, int k, int t0, int t1, int use_limit,
                      int limit_base);
