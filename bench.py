@@ -9,13 +9,16 @@ working buffers at the start of every step (the reduction overwrites them).
 
 Printed: one JSON line with the seconds per pencil, the effective TFLOP/s at
 the fixed flop count F(n) = 116 n^3 / 3 (leading-order flops of the blocked
-method with Q and Z, see DESIGN.md), the backward errors of the last step,
+method with Q and Z), the backward errors of the last step,
 the roofline of the dominant launch class, clocks sampled during the timed
 region, an end-to-end number through the C ABI with host buffers, and a CPU
 baseline (the unblocked Givens reduction of the CPU oracle on a bounded
 sample, extrapolated by n^3).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--n 16384] [--nb 32]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--n 16384] [--nb 32] [--precision emu|fp64]
+The default path is the emulated one (HT_PREC_EMU: the chain applications of
+the absorption as exact digit products on the tensor cores); --precision fp64
+times the native FP64 path on the same pencil.
   python bench.py --impl reference     # CPU oracle arm, bounded sample
 Multi-GPU (torchrun): independent replicas, one pencil per rank per step.
 """
@@ -39,7 +42,7 @@ FP64_PEAK_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12  # SMs x SMSPs x DFMA/clk x
 
 
 def f_nom(n: int) -> float:
-    """Leading-order flops of the blocked HouseHT with Q and Z (DESIGN.md)."""
+    """Leading-order flops of the blocked HouseHT with Q and Z."""
     return 116.0 * n ** 3 / 3.0
 
 
@@ -51,7 +54,7 @@ def parse():
     p.add_argument("--n", type=int, default=16384)
     p.add_argument("--nb", type=int, default=32)
     p.add_argument("--seed", type=int, default=3000)
-    p.add_argument("--precision", default="fp64", choices=["fp64", "emu"])
+    p.add_argument("--precision", default="emu", choices=["fp64", "emu"])
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--cpu-sample", type=int, default=1024)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -62,6 +65,40 @@ def parse():
 # ----------------------------------------------------------------------------
 # CPU oracle timing (the reference arm and the cpu_baseline key)
 # ----------------------------------------------------------------------------
+EMU_PAIRS = 27  # FP16 digit-pair products per FP64 multiply-add in the emulated sweeps (6 x 7 digits, levels <= 8)
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def roofline(cls: str, flops: float, ms: float, launches: int, precision: str) -> dict:
+    """Roofline of one launch class from the library's per-launch CUDA events:
+    the emulated sweeps against the measured dense 16-bit tensor peak (their
+    algorithmic work is EMU_PAIRS digit-pair products per FP64 multiply-add),
+    every other class against the FP64 DFMA peak (FP64 ALU bound)."""
+    sec = ms / 1e3
+    if cls == "sweep" and precision == "emu":
+        pk = measured_peaks()
+        peak = float(pk.get("bf16_tflops_sustained", 1700.0))
+        ach = EMU_PAIRS * flops / sec / 1e12 if sec > 0 else 0.0
+        return {"kernel_class": "sweep (emulated FP64, FP16 digit products on mma.sync)", "bound": "tensor",
+                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                "fp64_equivalent_tflops": flops / sec / 1e12 if sec > 0 else 0.0,
+                "launches": int(launches), "avg_launch_ms": ms / max(launches, 1),
+                "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops_sustained; FP16 dense has the BF16 rate)"}
+    ach = flops / sec / 1e12 if sec > 0 else 0.0
+    return {"kernel_class": cls, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "launches": int(launches),
+            "avg_launch_ms": ms / max(launches, 1),
+            "peak_source": "derived: FP64 DFMA units x max clock (152 SMs x 4 x 0.5 DFMA/clk x 2 x 2.07 GHz); "
+                           "a DFMA loop measured 1.19 TFLOP/s"}
+
+
 def cpu_oracle_time(n_sample: int, seed: int) -> tuple[float, float]:
     """Seconds of the oracle's unblocked Givens HT reduction (Q and Z) of one
     pencil of order n_sample, and its extrapolation to n by n^3."""
@@ -239,12 +276,9 @@ def run_ours(args):
     cls_n = agg["launches_by_class"]
     dom = max(range(7), key=lambda i: cls_ms[i])
     launches = sum(cls_n[:7])
-    ach = cls_fl[dom] / (cls_ms[dom] / 1e3) / 1e12 if cls_ms[dom] > 0 else 0.0
-    roof = {"kernel_class": ht.CLASS_NAMES[dom], "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-            "launches": int(cls_n[dom]), "avg_launch_ms": cls_ms[dom] / max(cls_n[dom], 1),
-            "peak_source": "FP64 DFMA units x max clock (152 SMs x 4 x 0.5 DFMA/clk x 2 x 2.07 GHz); "
-                           "measured DFMA loop 1.19 TFLOP/s"}
+    roof = roofline(ht.CLASS_NAMES[dom], cls_fl[dom], cls_ms[dom], cls_n[dom], args.precision)
+    by_class = {ht.CLASS_NAMES[i]: roofline(ht.CLASS_NAMES[i], cls_fl[i], cls_ms[i], cls_n[i], args.precision)
+                for i in range(6) if cls_ms[i] > 0}
 
     e2e = None
     if not args.no_e2e and rank == 0:
@@ -255,9 +289,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         A.copy_(A_host.view(n, n).t(), non_blocking=True)
         B.copy_(B_host.view(n, n).t(), non_blocking=True)
-        rc = ht.reduce_plain(n, A.data_ptr(), n, B.data_ptr(), n, Q.data_ptr(), Z.data_ptr(), 1, stream.cuda_stream)
-        if rc != 0:
-            raise RuntimeError(f"ht_reduce failed: {rc}")
+        ht.reduce(A, B, Q, Z, want_qz=True, opts=ht.options(nb=nb, precision=prec), stream=stream)
         for X in (A, B, Q, Z):
             H_host.view(n, n).t().copy_(X, non_blocking=True)
         torch.cuda.synchronize(dev)
@@ -283,7 +315,10 @@ def run_ours(args):
             "precision_path": args.precision,
             "config": {"workload": f"single pencil n={n}, A~N(0,1), B=triu(N(0,1))+4I, Q and Z accumulated",
                        "n": n, "nb": nb, "flop_count": "116 n^3 / 3",
-                       "l2": "inputs (2 x 2 GiB) exceed the 129 MB L2; no flush",
+                       "l2": (f"A, B, Q, Z ({n * n * 8 / 2**30:.2f} GiB each) exceed the 129 MB L2; no flush"
+                              if n * n * 8 > 129e6 else
+                              f"A, B, Q, Z ({n * n * 8 / 2**20:.1f} MiB each) do not all exceed L2; not flushed "
+                              "(not a headline size)"),
                        "parallelism": f"replicas x{world}"},
             "bwd_err": {"a": rep["bwd_a"], "b": rep["bwd_b"], "orth_q": rep["orth_q"], "orth_z": rep["orth_z"],
                         "structure_ok": rep["h_nonzeros_below_subdiag"] == 0 and rep["t_nonzeros_below_diag"] == 0,
@@ -292,6 +327,8 @@ def run_ours(args):
                       "ir_steps": agg["ir_steps"], "cols_with_ir": agg["cols_with_ir"],
                       "ms_by_class": dict(zip(ht.CLASS_NAMES[:7], cls_ms[:7]))},
             "roofline": roof,
+            "roofline_by_class": {k: {"bound": v["bound"], "achieved": v["achieved"], "frac": v["frac"]}
+                                  for k, v in by_class.items()},
             "clocks": clk,
             "gpu_launches": int(launches),
             "e2e": e2e,
