@@ -283,7 +283,8 @@ struct EmuSmem {
   static constexpr int XS = 2 * KPAD + 1;  // odd leading dimension of the FP64 stripe (per line)
   static constexpr size_t XF = (size_t)ER * XS * sizeof(double);
   static constexpr size_t XD = (size_t)EA * 2 * EmuDims<KPAD>::KS1 * 32 * sizeof(uint4);  // X digits; later P
-  static constexpr size_t PF = (size_t)ER * KPAD * sizeof(long long);
+  static constexpr int PLD = KPAD + 1;  // odd leading dimension of the int64 P buffer (no bank conflicts)
+  static constexpr size_t PF = (size_t)ER * PLD * sizeof(long long);
   static constexpr size_t PD = (size_t)EA * 2 * EmuDims<KPAD>::KS2 * 32 * sizeof(uint4);
   static constexpr size_t VW = (size_t)EmuDims<KPAD>::WIN * sizeof(uint2);
   static constexpr size_t BYTES = XF + XD + VW + 2 * ER * sizeof(int);
@@ -395,10 +396,10 @@ __global__ void __launch_bounds__(ETH) emu_sweep_kernel(EmuBatch b) {
     __syncthreads();
     if (wi < 2 * NT1) {
       const int r0 = (wi / NT1) * 16 + g, q0 = (wi % NT1) * 8 + 2 * tt;
-      Pf[r0 * KPAD + q0] = tp[0];
-      Pf[r0 * KPAD + q0 + 1] = tp[1];
-      Pf[(r0 + 8) * KPAD + q0] = tp[2];
-      Pf[(r0 + 8) * KPAD + q0 + 1] = tp[3];
+      Pf[r0 * M::PLD + q0] = tp[0];
+      Pf[r0 * M::PLD + q0 + 1] = tp[1];
+      Pf[(r0 + 8) * M::PLD + q0] = tp[2];
+      Pf[(r0 + 8) * M::PLD + q0 + 1] = tp[3];
     }
     __syncthreads();
     // per-line bit length of P
@@ -406,7 +407,7 @@ __global__ void __launch_bounds__(ETH) emu_sweep_kernel(EmuBatch b) {
       const int li = tid >> 3, part = tid & 7;
       unsigned long long mx = 0;
       for (int q = part; q < KPAD; q += 8) {
-        const long long v = Pf[li * KPAD + q];
+        const long long v = Pf[li * M::PLD + q];
         mx = max(mx, (unsigned long long)(v < 0 ? -v : v));
       }
       mx = max(mx, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)mx, 1));
@@ -423,7 +424,7 @@ __global__ void __launch_bounds__(ETH) emu_sweep_kernel(EmuBatch b) {
       for (int i = 0; i < 8; ++i) {
         const int li = m * 16 + g + 8 * ((i >> 1) & 1);
         const int q = ks * 16 + 2 * tt + (i & 1) + 8 * (i >> 2);
-        const long long v = Pf[li * KPAD + q];
+        const long long v = Pf[li * M::PLD + q];
         const int beta = Bs[li];
         long long y;
         if (beta <= 53) y = v * (1LL << (53 - beta));

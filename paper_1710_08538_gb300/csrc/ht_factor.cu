@@ -30,16 +30,18 @@ constexpr int MAXW = 2 * HT_NB_MAX;  // largest window height
 // Householder scalars of a column with pivot x0 and squared tail norm tail
 // (DLARFG rule): beta = (alpha - x0) / alpha, alpha = -sign(x0) ||x||,
 // scal = 1 / (x0 - alpha).
-__device__ __forceinline__ void house_scalars(double x0, double tail, double* sc) {
+// Called by lanes 0 and 1 of one warp: both quotients come out of one division
+// sequence (lane 0: beta = (alpha - x0) / alpha, lane 1: scal = 1 / (x0 - alpha)).
+__device__ __forceinline__ void house_scalars(double x0, double tail, double* sc, int lane) {
   if (tail == 0.0) {
-    sc[0] = 0.0; sc[1] = x0; sc[2] = 0.0;
+    if (lane == 0) { sc[0] = 0.0; sc[1] = x0; sc[2] = 0.0; }
     return;
   }
   const double nr = sqrt(x0 * x0 + tail);
   const double alpha = (x0 >= 0.0) ? -nr : nr;
-  sc[0] = (alpha - x0) / alpha;
-  sc[1] = alpha;
-  sc[2] = 1.0 / (x0 - alpha);
+  const double q = (lane == 0 ? alpha - x0 : 1.0) / (lane == 0 ? alpha : x0 - alpha);
+  if (lane == 0) { sc[0] = q; sc[1] = alpha; }
+  else sc[2] = q;
 }
 
 // Householder QR (ql = false) or QL (ql = true) of the w x kk column-major
@@ -50,6 +52,24 @@ __device__ __forceinline__ void house_scalars(double x0, double tail, double* sc
 // reflector scalars (double-buffered in sc) while warps 1.. update the other
 // columns four at a time with a packed cross-lane reduction.  bv (w entries)
 // holds beta * v.  Two block barriers per reflector.
+
+// sums of four per-lane partials over a warp, every lane receives all four
+__device__ __forceinline__ void warp_sum4(double d[4], int lane) {
+  const bool b16 = lane & 16, b8 = lane & 8;
+  double s0 = b16 ? d[2] : d[0], s1 = b16 ? d[3] : d[1];
+  const double o0 = __shfl_xor_sync(0xffffffffu, b16 ? d[0] : d[2], 16);
+  const double o1 = __shfl_xor_sync(0xffffffffu, b16 ? d[1] : d[3], 16);
+  s0 += o0;
+  s1 += o1;
+  double sv = b8 ? s1 : s0;
+  sv += __shfl_xor_sync(0xffffffffu, b8 ? s0 : s1, 8);
+  sv += __shfl_xor_sync(0xffffffffu, sv, 4);
+  sv += __shfl_xor_sync(0xffffffffu, sv, 2);
+  sv += __shfl_xor_sync(0xffffffffu, sv, 1);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) d[i] = __shfl_sync(0xffffffffu, sv, 16 * (i >> 1) + 8 * (i & 1));
+}
+
 __device__ void house_factor(double* X, int w, int kk, bool ql, double* Vs, double* tau, double* sc, double* bv) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   for (int e = tid; e < w * kk; e += blockDim.x) Vs[e] = 0.0;
@@ -60,7 +80,7 @@ __device__ void house_factor(double* X, int w, int kk, bool ql, double* Vs, doub
     for (int r = lo + lane; r < hi; r += 32)
       if (r != t) s += X[r + c * w] * X[r + c * w];
     s = ht_warp_sum(s);
-    if (lane == 0) house_scalars(X[t + c * w], s, sc);
+    if (lane < 2) house_scalars(X[t + c * w], s, sc, lane);
   }
   __syncthreads();
   for (int q = 0; q < kk; ++q) {
@@ -96,7 +116,7 @@ __device__ void house_factor(double* X, int w, int kk, bool ql, double* Vs, doub
           if (r != t2) sq += X[r + cnext * w] * X[r + cnext * w];
         sq = ht_warp_sum(sq);
         __syncwarp();
-        if (lane == 0) house_scalars(X[t2 + cnext * w], sq, nxt);
+        if (lane < 2) house_scalars(X[t2 + cnext * w], sq, nxt, lane);
       }
     } else if (beta != 0.0) {
       for (int g0 = cb + 4 * (wid - 1); g0 < ce; g0 += 4 * (nw - 1)) {
@@ -107,19 +127,7 @@ __device__ void house_factor(double* X, int w, int kk, bool ql, double* Vs, doub
           for (int i = 0; i < 4; ++i)
             if (g0 + i < ce && g0 + i != cnext) d[i] += vr * X[r + (g0 + i) * w];
         }
-        const bool b16 = lane & 16, b8 = lane & 8;
-        double s0 = b16 ? d[2] : d[0], s1 = b16 ? d[3] : d[1];
-        const double o0 = __shfl_xor_sync(0xffffffffu, b16 ? d[0] : d[2], 16);
-        const double o1 = __shfl_xor_sync(0xffffffffu, b16 ? d[1] : d[3], 16);
-        s0 += o0;
-        s1 += o1;
-        double sv = b8 ? s1 : s0;
-        sv += __shfl_xor_sync(0xffffffffu, b8 ? s0 : s1, 8);
-        sv += __shfl_xor_sync(0xffffffffu, sv, 4);
-        sv += __shfl_xor_sync(0xffffffffu, sv, 2);
-        sv += __shfl_xor_sync(0xffffffffu, sv, 1);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) d[i] = __shfl_sync(0xffffffffu, sv, 16 * (i >> 1) + 8 * (i & 1));
+        warp_sum4(d, lane);
         for (int r = lo + lane; r < hi; r += 32) {
           const double br = bv[r];
 #pragma unroll
@@ -140,6 +148,7 @@ __device__ void form_t(const double* Vs, const double* tau, int w, int kk, doubl
   const int tid = threadIdx.x;
   for (int e = tid; e < kk * kk; e += blockDim.x) {
     const int a = e % kk, b = e / kk;
+    Tm[e] = (a == b) ? tau[a] : 0.0;
     double d0 = 0.0, d1 = 0.0;
     if (a < b) {
       int r = 0;
@@ -150,7 +159,6 @@ __device__ void form_t(const double* Vs, const double* tau, int w, int kk, doubl
       if (r < w) d0 += Vs[r + a * w] * Vs[r + b * w];
     }
     Gm[e] = d0 + d1;
-    Tm[e] = (a == b) ? tau[a] : 0.0;
   }
   __syncthreads();
   for (int h = 1; h < kk; h *= 2) {
@@ -300,18 +308,20 @@ __device__ __forceinline__ unsigned long long rs_now() {
 
 // right: X(lines [l0, l1), o0 .. o0+w) <- X G = X - (X V) T V^T;
 // left:  X(o0 .. o0+w, lines) <- G^T X = X - V T^T (V^T X);
-// stripes of SRR lines distributed over all CTAs except `skip`.
+// stripes of SRR lines distributed over `nact` CTAs, this one being `rank`
+// (stripes rank, rank + nact, ...).  A CTA with stripes first stages V
+// (w x kr) and T (kr x kr) in shared memory (Vsm, Tsm) so that the products
+// read no global memory in their inner loops.
 constexpr int SRR = 8;
 __device__ void apply_vt(bool right, double* X, long ldx, int l0, int l1, int o0, int w, int kr, const double* Vw,
-                         const double* Tg, double* Xs, double* Ps, double* P2, int skip) {
+                         const double* Tg, double* Xs, double* Ps, double* P2, double* Vsm, double* Tsm, int rank,
+                         int nact) {
   const int tid = threadIdx.x;
   const int nstripes = (l1 - l0 + SRR - 1) / SRR;
-  const int nact = (skip >= 0 && (int)gridDim.x > 1) ? gridDim.x - 1 : gridDim.x;
-  int rank = blockIdx.x;
-  if (skip >= 0 && (int)gridDim.x > 1) {
-    if ((int)blockIdx.x == skip) return;
-    if ((int)blockIdx.x > skip) --rank;
-  }
+  if (rank < 0 || rank >= nstripes) return;
+  for (int e = tid; e < w * kr; e += blockDim.x) Vsm[e] = __ldcg(Vw + e);
+  for (int e = tid; e < kr * kr; e += blockDim.x) Tsm[e] = __ldcg(Tg + e);
+  __syncthreads();
   for (int sidx = rank; sidx < nstripes; sidx += nact) {
     const int sb = l0 + sidx * SRR, lines = min(SRR, l1 - sb);
     // stripe in shared memory column-major by line (Xs[li + c * SRR]): the
@@ -331,10 +341,10 @@ __device__ void apply_vt(bool right, double* X, long ldx, int l0, int l1, int o0
       double s0 = 0.0, s1 = 0.0;
       int c = 0;
       for (; c + 1 < w; c += 2) {
-        s0 += Xs[li + c * SRR] * __ldcg(Vw + c + (size_t)q * w);
-        s1 += Xs[li + (c + 1) * SRR] * __ldcg(Vw + c + 1 + (size_t)q * w);
+        s0 += Xs[li + c * SRR] * Vsm[c + q * w];
+        s1 += Xs[li + (c + 1) * SRR] * Vsm[c + 1 + q * w];
       }
-      if (c < w) s0 += Xs[li + c * SRR] * __ldcg(Vw + c + (size_t)q * w);
+      if (c < w) s0 += Xs[li + c * SRR] * Vsm[c + q * w];
       Ps[li + q * SRR] = s0 + s1;
     }
     __syncthreads();
@@ -342,17 +352,22 @@ __device__ void apply_vt(bool right, double* X, long ldx, int l0, int l1, int o0
     for (int e = tid; e < SRR * kr; e += blockDim.x) {
       const int li = e % SRR, q = e / SRR;
       double s0 = 0.0;
-      for (int l = 0; l <= q; ++l) s0 += Ps[li + l * SRR] * __ldcg(Tg + l + (size_t)q * kr);
+      for (int l = 0; l <= q; ++l) s0 += Ps[li + l * SRR] * Tsm[l + q * kr];
       P2[li + q * SRR] = s0;
     }
     __syncthreads();
     for (int e = tid; e < SRR * w; e += blockDim.x) {
       const int li = e % SRR, c = e / SRR;
       if (li >= lines) continue;
-      double s0 = Xs[li + c * SRR];
-      for (int q = 0; q < kr; ++q) s0 -= P2[li + q * SRR] * __ldcg(Vw + c + (size_t)q * w);
-      if (right) X[(size_t)(sb + li) + (size_t)(o0 + c) * ldx] = s0;
-      else X[(size_t)(o0 + c) + (size_t)(sb + li) * ldx] = s0;
+      double s0 = Xs[li + c * SRR], s1 = 0.0;
+      int q = 0;
+      for (; q + 1 < kr; q += 2) {
+        s0 -= P2[li + q * SRR] * Vsm[c + q * w];
+        s1 -= P2[li + (q + 1) * SRR] * Vsm[c + (q + 1) * w];
+      }
+      if (q < kr) s0 -= P2[li + q * SRR] * Vsm[c + q * w];
+      if (right) X[(size_t)(sb + li) + (size_t)(o0 + c) * ldx] = s0 + s1;
+      else X[(size_t)(o0 + c) + (size_t)(sb + li) * ldx] = s0 + s1;
     }
     __syncthreads();
   }
@@ -426,8 +441,11 @@ __global__ void __launch_bounds__(HT_THREADS, 1) restore_kernel(RestoreArgs a) {
       __syncthreads();
       form_w(f.Vs, f.Tm, width, kr, Ww);
     } else {
-      if (right) apply_vt(true, a.B, a.ldb, j1, j1 + lim, j1 + off, width, kr, Vw, Tg, Xs, Ps, P2, wcta);
-      else apply_vt(false, a.B, a.ldb, j1 + lim, a.n, j1 + off, width, kr, Vw, Tg, Xs, Ps, P2, wcta);
+      // every CTA but the one forming Ww
+      const int nact = (wcta != 0) ? (int)gridDim.x - 1 : (int)gridDim.x;
+      const int rank = ((int)blockIdx.x > wcta && wcta != 0) ? (int)blockIdx.x - 1 : (int)blockIdx.x;
+      if (right) apply_vt(true, a.B, a.ldb, j1, j1 + lim, j1 + off, width, kr, Vw, Tg, Xs, Ps, P2, f.Vs, f.Gm, rank, nact);
+      else apply_vt(false, a.B, a.ldb, j1 + lim, a.n, j1 + off, width, kr, Vw, Tg, Xs, Ps, P2, f.Vs, f.Gm, rank, nact);
     }
     grid.sync();
     if (a.ptime && blockIdx.x == 0 && threadIdx.x == 0) a.ptime[19] += rs_now() - tw0;
@@ -458,6 +476,157 @@ __global__ void __launch_bounds__(HT_THREADS, 1) restore_kernel(RestoreArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Restore chains with the application overlapped (grids of >= 6 CTAs).  The
+// step-t transform G_t has to reach every line on the far side of the factored
+// block (rows above for the RQ restore, columns to the right for the QR one),
+// but step t + 1 only needs it on the lines of the next block.  So one grid
+// barrier per step:
+//   phase 1 (iteration t): CTA 0 factors step t (after the helpers have
+//           brought the next block up to date, see phase 2) and forms T_t;
+//           CTA 1 forms Ww_{t-1}; CTAs 2.. apply G_{t-1} to the lines beyond
+//           step t-1's next block;
+//   grid barrier;
+//   phase 2: CTAs 2..5 apply G_t to the next block (8 lines each) and count
+//           (hcount); CTA 0 starts the next factorization when all four have.
+// Each line still takes G_0, G_1, ... in order: the lines beyond a next block
+// get G_{t-1} in phase 1 of iteration t and the block that becomes next at
+// step t gets G_t only after that phase's barrier.
+// ---------------------------------------------------------------------------
+constexpr int RS_HELP = 4;
+
+struct SplitArgs {
+  int mode, p, k, j, n;
+  double* B;
+  long ldb;
+  double* wy;
+  size_t stride;
+  double* tstore;
+  int* hcount;  // helper completions (zeroed by the launcher)
+  int* err;     // device error word (HT_ERR_TIMEOUT if the wait for the helpers gave up)
+  unsigned long long* ptime;
+};
+
+// step s: window [off, off + width), nrefl kr, factored lines start f0, next block [n0, n1)
+// (empty when none), lines beyond the next block [b0, b1); all relative to j + 1
+struct SplitStep {
+  int off, width, kr, f0, n0, n1, b0, b1;
+};
+__device__ __forceinline__ SplitStep split_step(bool right, int p, int k, int s) {
+  SplitStep g;
+  if (right) {
+    const int bb = ht_num_right_blocks(p, k) - 1 - s;
+    int c0, c1, d0, d1;
+    ht_right_block(p, k, bb - 1, &c0, &c1);
+    ht_right_block(p, k, bb, &d0, &d1);
+    g.off = c0; g.width = d1 - c0; g.kr = d1 - d0; g.f0 = d0;
+    g.n0 = c0; g.n1 = c1; g.b0 = 0; g.b1 = c0;
+  } else {
+    const int nlb = ht_num_left_blocks(p, k);
+    int r0, r1, e0, e1;
+    ht_left_block(p, k, s, &r0, &r1);
+    if (s + 1 < nlb) ht_left_block(p, k, s + 1, &e0, &e1); else { e0 = r1; e1 = r1; }
+    g.off = r0; g.width = e1 - r0; g.kr = r1 - r0; g.f0 = r0;
+    g.n0 = e0; g.n1 = e1; g.b0 = e1; g.b1 = p;
+  }
+  return g;
+}
+
+__global__ void __launch_bounds__(HT_THREADS, 1) restore_split_kernel(SplitArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ double sm[];
+  __shared__ int ok;
+  FSm f = fsm(sm);
+  double* Xs = f.Tm;  // stripe buffers reuse Tm, Gm, scr
+  double* Ps = Xs + SRR * MAXW;
+  double* P2 = Ps + SRR * HT_NB_MAX;
+  const int p = a.p, k = a.k, j1 = a.j + 1;
+  const bool right = (a.mode == 2);
+  const int nsteps = right ? ht_num_right_blocks(p, k) - 1 : ht_num_left_blocks(p, k);
+  const int cta = blockIdx.x, tid = threadIdx.x;
+  bool failed = false;  // CTA 0 only: a timed-out wait; it keeps joining the barriers
+  for (int t = 0; t <= nsteps; ++t) {
+    // ---- phase 1 ----
+    if (cta == 0 && t < nsteps) {
+      if (t > 0 && !failed) {
+        if (tid == 0) {
+          const unsigned long long tw = a.ptime ? rs_now() : 0ull;
+          ok = 1;
+          if (ht_ld_acquire(a.hcount) < RS_HELP * t) {
+            ok = 0;
+            for (long it = 0; it < (long)HT_SPIN_LIMIT; ++it) {
+              __nanosleep(64);
+              if (ht_ld_acquire(a.hcount) >= RS_HELP * t) { ok = 1; break; }
+            }
+            if (!ok) atomicCAS(a.err, 0, HT_ERR_TIMEOUT);
+          }
+          if (a.ptime) a.ptime[18] += rs_now() - tw;
+        }
+        __syncthreads();
+        failed = !ok;
+      }
+      if (!failed) {
+        const SplitStep g = split_step(right, p, k, t);
+        const int w = g.width, kr = g.kr;
+        double* blk = right ? a.B + (size_t)(j1 + g.f0) + (size_t)(j1 + g.off) * a.ldb
+                            : a.B + (size_t)(j1 + g.off) + (size_t)(j1 + g.off) * a.ldb;
+        for (int e = tid; e < w * kr; e += blockDim.x) {
+          const int r = e % w, c = e / w;
+          f.X[e] = right ? __ldcg(blk + (size_t)c + (size_t)r * a.ldb) : __ldcg(blk + (size_t)r + (size_t)c * a.ldb);
+        }
+        __syncthreads();
+        const unsigned long long t0 = (a.ptime && tid == 0) ? rs_now() : 0ull;
+        house_factor(f.X, w, kr, right, f.Vs, f.tau, f.nrm, f.bv);
+        const unsigned long long t1 = (a.ptime && tid == 0) ? rs_now() : 0ull;
+        form_t(f.Vs, f.tau, w, kr, f.Tm, f.Gm, f.scr);
+        if (a.ptime && tid == 0) {
+          const unsigned long long t2 = rs_now();
+          a.ptime[16] += t1 - t0;
+          a.ptime[17] += t2 - t1;
+        }
+        double* Vw = a.wy + (size_t)t * a.stride;
+        double* Tg = a.tstore + (size_t)t * k * k;
+        for (int e = tid; e < w * kr; e += blockDim.x) {
+          const int r = e % w, c = e / w;
+          if (right) blk[(size_t)c + (size_t)r * a.ldb] = f.X[e];
+          else blk[(size_t)r + (size_t)c * a.ldb] = f.X[e];
+          Vw[e] = f.Vs[e];
+        }
+        for (int e = tid; e < kr * kr; e += blockDim.x) Tg[e] = f.Tm[e];
+        __threadfence();
+      }
+    } else if (cta == 1 && t > 0) {
+      // Ww = Vw T^T of step t - 1 for the later sweeps
+      const SplitStep g = split_step(right, p, k, t - 1);
+      const double* Vw = a.wy + (size_t)(t - 1) * a.stride;
+      const double* Tg = a.tstore + (size_t)(t - 1) * k * k;
+      for (int e = tid; e < g.width * g.kr; e += blockDim.x) f.Vs[e] = __ldcg(Vw + e);
+      for (int e = tid; e < g.kr * g.kr; e += blockDim.x) f.Tm[e] = __ldcg(Tg + e);
+      __syncthreads();
+      form_w(f.Vs, f.Tm, g.width, g.kr, a.wy + (size_t)(t - 1) * a.stride + a.stride / 2);
+    } else if (cta >= 2 && t > 0) {
+      // G_{t-1} to the lines beyond step t-1's next block
+      const SplitStep g = split_step(right, p, k, t - 1);
+      const unsigned long long t0 = (a.ptime && cta == 2 && tid == 0) ? rs_now() : 0ull;
+      apply_vt(right, a.B, a.ldb, j1 + g.b0, j1 + g.b1, j1 + g.off, g.width, g.kr, a.wy + (size_t)(t - 1) * a.stride,
+               a.tstore + (size_t)(t - 1) * k * k, Xs, Ps, P2, f.Vs, f.Gm, cta - 2, (int)gridDim.x - 2);
+      if (a.ptime && cta == 2 && tid == 0) a.ptime[19] += rs_now() - t0;
+    }
+    if (t == nsteps) break;
+    grid.sync();
+    // ---- phase 2: G_t to the next block ----
+    if (cta >= 2 && cta < 2 + RS_HELP) {
+      const SplitStep g = split_step(right, p, k, t);
+      if (g.n1 > g.n0)
+        apply_vt(right, a.B, a.ldb, j1 + g.n0, j1 + g.n1, j1 + g.off, g.width, g.kr, a.wy + (size_t)t * a.stride,
+                 a.tstore + (size_t)t * k * k, Xs, Ps, P2, f.Vs, f.Gm, cta - 2, RS_HELP);
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) atomicAdd(a.hcount, 1);
+    }
+  }
+}
+
 }  // namespace
 
 static int g_factor_attr = 0;
@@ -467,6 +636,7 @@ static void set_factor_attr() {
   cudaFuncSetAttribute(chains_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   cudaFuncSetAttribute(form_wy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   cudaFuncSetAttribute(restore_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(restore_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   g_factor_attr = 1;
 }
 
@@ -483,14 +653,22 @@ cudaError_t ht_launch_chains(cudaStream_t st, double* V2, double* U2, long ld, i
 }
 
 cudaError_t ht_launch_restore(cudaStream_t st, int mode, int p, int k, int j, int n, double* B, long ldb, double* wy,
-                              size_t stride, double* tstore, unsigned long long* ptime) {
+                              size_t stride, double* tstore, int* hcount, int* err, unsigned long long* ptime) {
   set_factor_attr();
   const int nsteps = (mode == 2) ? ht_num_right_blocks(p, k) - 1 : ht_num_left_blocks(p, k);
   if (nsteps <= 0) return cudaSuccess;
-  RestoreArgs a{mode, p, k, j, n, B, ldb, wy, stride, tstore, ptime};
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms >= 2 + RS_HELP && hcount && err) {
+    cudaError_t e = cudaMemsetAsync(hcount, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    SplitArgs sa{mode, p, k, j, n, B, ldb, wy, stride, tstore, hcount, err, ptime};
+    void* sargs[] = {&sa};
+    return cudaLaunchCooperativeKernel((void*)restore_split_kernel, dim3(sms), dim3(HT_THREADS), sargs,
+                                       factor_smem_doubles() * sizeof(double), st);
+  }
+  RestoreArgs a{mode, p, k, j, n, B, ldb, wy, stride, tstore, ptime};
   void* args[] = {&a};
   return cudaLaunchCooperativeKernel((void*)restore_kernel, dim3(sms), dim3(HT_THREADS), args,
                                      factor_smem_doubles() * sizeof(double), st);
