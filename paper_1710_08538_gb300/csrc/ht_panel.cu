@@ -150,6 +150,42 @@ __device__ void tile_gemv(const double* M, long ld, int r0, int rows, int c0, in
   __syncthreads();
 }
 
+// Row tile of a GEMV streamed from memory: returns, to thread r < rows (<= 32),
+// sum_c M(r0 + r, c0 + c) x[c] over c < cols.  Lanes take rows (coalesced:
+// consecutive rows of a column are contiguous), the warps take interleaved
+// columns, eight columns per step so that eight loads per thread are in
+// flight; x is read from global memory (XG, every lane the same address) or
+// shared memory.  red: blockDim.x doubles of shared scratch.  Two barriers.
+template <bool XG>
+__device__ double gemv32(const double* M, long ld, int r0, int rows, int c0, int cols, const double* x, double* red) {
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double a0 = 0.0, a1 = 0.0;
+  if (lane < rows) {
+    const double* p = M + (size_t)(r0 + lane) + (size_t)c0 * ld;
+    for (int c = wi; c < cols; c += 8 * nw) {
+      double mv[8], xv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int cc = c + u * nw;
+        mv[u] = (cc < cols) ? __ldcg(p + (size_t)cc * ld) : 0.0;
+        xv[u] = (cc < cols) ? (XG ? __ldcg(x + cc) : x[cc]) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        a0 += mv[u] * xv[u];
+        a1 += mv[u + 1] * xv[u + 1];
+      }
+    }
+  }
+  red[threadIdx.x] = a0 + a1;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32)
+    for (int w2 = 0; w2 < nw; ++w2) t += red[w2 * 32 + threadIdx.x];
+  __syncthreads();
+  return t;
+}
+
 constexpr int BI = HT_TRSV_BI;  // diagonal block of the grid-synchronous solve
 
 // Inverse of the upper triangular bs x bs diagonal block D = B_loc[r0.., r0..]
@@ -359,14 +395,9 @@ __device__ void trsv_gs(const PanelArgs& a, Grid& grid, int m, const double* rhs
       for (int q = tid; q < BI; q += blockDim.x) xs[q] = (q < rows) ? __ldcg(sol + r0 + q) : 0.0;
       __syncthreads();
       const int ch = (r0 + G - 1) / G, rb = min(r0, cta * ch), re = min(r0, rb + ch);
-      for (int tb = rb; tb < re; tb += BS) {
-        const int tr = min(BS, re - tb);
-        double sum = 0.0;
-        for (int cc = 0; cc < rows; cc += BS) {
-          tile_gemv(Bl, ldb, tb, tr, r0 + cc, min(BS, rows - cc), xs + cc, red4, red4);
-          if (tid < BS) sum += red4[tid];
-          __syncthreads();
-        }
+      for (int tb = rb; tb < re; tb += 32) {
+        const int tr = min(32, re - tb);
+        const double sum = gemv32<false>(Bl, ldb, tb, tr, r0, rows, xs, red4);
         if (tid < tr) {
           const double av = __ldcg(accv + tb + tid);
           accv[tb + tid] = ldexp(av, sh_acc) - ldexp(sum, sh_x);
@@ -657,24 +688,18 @@ __global__ void __launch_bounds__(HT_THREADS, 1) panel_kernel(PanelArgs a) {
       // rb * BS < (ch + 1) * CWC, assigned round-robin to CTAs
       {
         constexpr int CWC = 4 * BS;
+        constexpr int RPC = CWC / 32;  // 32-row tiles per column chunk on the diagonal
         const double* Bl = a.B + (size_t)(s + 1) + (size_t)(s + 1) * a.ldb;
-        const int nrb = (m + BS - 1) / BS, nchk = (m + CWC - 1) / CWC;
+        const int nrb = (m + 31) / 32, nchk = (m + CWC - 1) / CWC;
         int total = 0;
-        for (int ch = 0; ch < nchk; ++ch) total += min(nrb, 4 * (ch + 1));
+        for (int ch = 0; ch < nchk; ++ch) total += min(nrb, RPC * (ch + 1));
         int ch = 0, base = 0;
         for (int item = cta; item < total; item += G) {
-          while (item >= base + min(nrb, 4 * (ch + 1))) { base += min(nrb, 4 * (ch + 1)); ++ch; }
+          while (item >= base + min(nrb, RPC * (ch + 1))) { base += min(nrb, RPC * (ch + 1)); ++ch; }
           const int rb = item - base;
-          const int r0 = rb * BS, rows = min(BS, m - r0);
-          double sum = 0.0;
-          for (int cc = ch * CWC; cc < min(m, (ch + 1) * CWC); cc += BS) {
-            const int cols = min(BS, m - cc);
-            if (tid < BS) xl[tid] = (tid < cols) ? __ldcg(a.w + cc + tid) : 0.0;
-            __syncthreads();
-            tile_gemv(Bl, a.ldb, r0, rows, cc, cols, xl, red4, red4);
-            if (tid < BS) sum += red4[tid];
-            __syncthreads();
-          }
+          const int r0 = rb * 32, rows = min(32, m - r0);
+          const int cc = ch * CWC, cols = min(CWC, m - cc);
+          const double sum = gemv32<true>(Bl, a.ldb, r0, rows, cc, cols, a.w + cc, red4);
           if (tid < rows) a.wpart[(size_t)ch * n + r0 + tid] = sum;
         }
       }
@@ -777,27 +802,20 @@ __global__ void __launch_bounds__(HT_THREADS, 1) panel_kernel(PanelArgs a) {
     PHASE_MARK(12);
     // ---- Phase O: GEMV partials A(s+1:n, j+1:n) v(k:m) ----
     {
+      // items: (32-row block, column chunk), about 8 per CTA for balance
       const int p = m - k;  // columns j+1..n-1
-      const int nrb = (m + BS - 1) / BS;
-      int nch = (2 * G + nrb - 1) / nrb;
+      const int nrb = (m + 31) / 32;
+      int nch = (8 * G + nrb - 1) / nrb;
       nch = max(1, min(nch, a.ychunks));
       const int cw = (p + nch - 1) / nch;
       const double* Ab = a.A + (size_t)(s + 1) + (size_t)(j + 1) * a.lda;
       const double* vk = a.z + k;  // v(k + c) for column j+1+c
       for (int item = cta; item < nrb * nch; item += G) {
         const int rb = item % nrb, ch = item / nrb;
-        const int r0 = rb * BS, rows = min(BS, m - r0);
-        const int c0 = ch * cw, cols = min(cw, p - c0);
-        double sum = 0.0;
-        for (int cc = 0; cc < cols; cc += BS) {
-          const int cn = min(BS, cols - cc);
-          if (tid < BS) xl[tid] = (tid < cn) ? __ldcg(vk + c0 + cc + tid) : 0.0;
-          __syncthreads();
-          tile_gemv(Ab, a.lda, r0, rows, c0 + cc, cn, xl, red4, red4);
-          if (tid < BS) sum += red4[tid];
-          __syncthreads();
-        }
-        if (tid < rows) a.ypart[(size_t)ch * n + r0 + tid] = (cols > 0) ? sum : 0.0;
+        const int r0 = rb * 32, rows = min(32, m - r0);
+        const int c0 = ch * cw, cols = max(0, min(cw, p - c0));
+        const double sum = gemv32<true>(Ab, a.lda, r0, rows, c0, cols, vk + c0, red4);
+        if (tid < rows) a.ypart[(size_t)ch * n + r0 + tid] = sum;
       }
       // chunks never visited for a row stay unused: the reduction below reads nch chunks
       if (tid == 0) shi[3] = nch;
