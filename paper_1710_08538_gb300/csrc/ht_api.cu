@@ -89,6 +89,7 @@ size_t ht_layout_work(HtWork& w, char* b, int n, int nb, int G, unsigned long lo
   const size_t oEmu = take(emu_win ? (emu_win * w.emu_cap + sizeof(double) - 1) / sizeof(double) : 0);
   const size_t oEmuE = take((size_t)w.emu_cap);
   const size_t oRc = take(2);
+  const size_t oRt = take(nn + 2 * HT_NB_MAX);
   if (!b) return total;
   w.U = (double*)(b + oU); w.V = (double*)(b + oV); w.Y = (double*)(b + oY);
   w.S = (double*)(b + oS); w.T = (double*)(b + oT);
@@ -119,6 +120,7 @@ size_t ht_layout_work(HtWork& w, char* b, int n, int nb, int G, unsigned long lo
   w.emu_dig = emu_win ? (void*)(b + oEmu) : nullptr;
   w.emu_exps = (int*)(b + oEmuE);
   w.rcount = (int*)(b + oRc);
+  w.rtaus = (double*)(b + oRt);
   w.wpart = (double*)(b + oWpart);
   w.tstore = (double*)(b + oTst);
   if (pt) *pt = (unsigned long long*)(b + oPt);
@@ -351,7 +353,7 @@ cudaError_t absorb(Ctx& c, int s, int k) {
       ht_right_block(p, k, bb, &d0, &d1);
       fl += fl_window(d1 - c0, d1 - d0) + 4.0 * (j + 1 + d0) * (d1 - c0) * (d1 - d0);
     }
-    if (nbr > 1) LAUNCH(HT_CLASS_RESTORE, fl, ht_launch_restore(st, 2, p, k, j, n, B, ldb, w.wyRR, wst, w.tstore, w.rcount, w.err, w.ptime));
+    if (nbr > 1) LAUNCH(HT_CLASS_RESTORE, fl, ht_launch_restore(st, 2, p, k, j, n, B, ldb, w.wyRR, wst, w.tstore, w.rtaus, w.rcount, w.err, w.ptime));
   }
   if (nbr > 1) {
     // rows 0..j of B, all rows of A and Z, one fused launch
@@ -409,7 +411,7 @@ cudaError_t absorb(Ctx& c, int s, int k) {
       if (t + 1 < nlb) ht_left_block(p, k, t + 1, &e0, &e1); else e1 = r1;
       fl += fl_window(e1 - r0, r1 - r0) + 4.0 * (n - (j + 1 + r1)) * (e1 - r0) * (r1 - r0);
     }
-    LAUNCH(HT_CLASS_RESTORE, fl, ht_launch_restore(st, 3, p, k, j, n, B, ldb, w.wyLR, wst, w.tstore, w.rcount, w.err, w.ptime));
+    LAUNCH(HT_CLASS_RESTORE, fl, ht_launch_restore(st, 3, p, k, j, n, B, ldb, w.wyLR, wst, w.tstore, w.rtaus, w.rcount, w.err, w.ptime));
   }
   {
     const HtSweepJob jobs[2] = {{A, lda, 0, j, n - j, j + 1, 0, 0}, {Q, ldq, 1, 0, c.want_qz ? n : 0, j + 1, 0, 0}};

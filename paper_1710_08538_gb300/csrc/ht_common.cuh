@@ -129,7 +129,8 @@ struct HtWork {
   double* xmax;            // per-CTA max |x| partials
   double* wpart;           // chunk partials of the triangular multiply
   double* tstore;          // T factors of the restore steps (HT_NB_MAX^2 each)
-  int* rcount;             // completion counter of the restore's next-block helpers
+  int* rcount;             // restore: reflectors published (a step-stamped counter)
+  double* rtaus;           // tau of every restore step (n + 2 HT_NB_MAX)
   void* emu_dig;           // digits of Vw / Ww for the emulated sweeps (emu_cap windows)
   int* emu_exps;           // their exponent bounds (2 per window)
   int emu_cap;             // windows per launch of the emulated sweeps
@@ -156,7 +157,8 @@ cudaError_t ht_launch_chains(cudaStream_t st, double* V2, double* U2, long ld, i
                              size_t stride, double* L1, double* R1);
 // restore chain of B (mode 2: RQ right, mode 3: QR left), one cooperative launch
 cudaError_t ht_launch_restore(cudaStream_t st, int mode, int p, int k, int j, int n, double* B, long ldb, double* wy,
-                              size_t stride, double* tstore, int* hcount, int* err, unsigned long long* ptime);
+                              size_t stride, double* tstore, double* taus, int* flag, int* err,
+                              unsigned long long* ptime);
 // One target of a fused chain application (see ht_apply.cu).
 #define HT_SWEEP_MAXJOBS 4
 struct HtSweepJob {

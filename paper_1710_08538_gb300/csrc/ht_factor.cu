@@ -70,8 +70,20 @@ __device__ __forceinline__ void warp_sum4(double d[4], int lane) {
   for (int i = 0; i < 4; ++i) d[i] = __shfl_sync(0xffffffffu, sv, 16 * (i >> 1) + 8 * (i & 1));
 }
 
-__device__ void house_factor(double* X, int w, int kk, bool ql, double* Vs, double* tau, double* sc, double* bv) {
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+// Optional publication of each reflector as soon as it is formed: v_q to
+// gV(:, q) (ld w), tau_q to gTau[q], then flag = base + q + 1 (release), all by
+// the last warp of the block, which then takes no column updates.
+struct HousePub {
+  double* gV;
+  double* gTau;
+  int* flag;
+  int base;
+};
+
+__device__ void house_factor(double* X, int w, int kk, bool ql, double* Vs, double* tau, double* sc, double* bv,
+                             const HousePub* pub = nullptr) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int nw = (blockDim.x >> 5) - (pub ? 1 : 0);  // warps that take part in the factorization
   for (int e = tid; e < w * kk; e += blockDim.x) Vs[e] = 0.0;
   if (wid == 0) {
     const int c = ql ? kk - 1 : 0, t = ql ? w - kk + c : c;
@@ -97,6 +109,16 @@ __device__ void house_factor(double* X, int w, int kk, bool ql, double* Vs, doub
     }
     if (tid == 0) tau[q] = beta;
     __syncthreads();
+    if (pub && wid == nw) {
+      // publisher warp: reflector q to global memory, then its flag
+      for (int r = lane; r < w; r += 32) pub->gV[r + (size_t)q * w] = Vs[r + q * w];
+      if (lane == 0) pub->gTau[q] = tau[q];
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) ht_st_release(pub->flag, pub->base + q + 1);
+      __syncthreads();
+      continue;
+    }
     const int cb = ql ? 0 : c + 1, ce = ql ? c : kk;
     const int cnext = (q + 1 < kk) ? (ql ? c - 1 : c + 1) : -1;
     if (wid == 0) {
@@ -143,9 +165,21 @@ __device__ void house_factor(double* X, int w, int kk, bool ql, double* Vs, doub
 
 // T (kk x kk upper, ld kk) with Vs T Vs^T = I - H_0 H_1 ... by recursive
 // halving: T = [T1, -T1 (V1^T V2) T2; 0, T2] (eq. (1) applied blockwise).
-// Gm (kk x kk) receives V^T V; scr holds kk*kk doubles.
-__device__ void form_t(const double* Vs, const double* tau, int w, int kk, double* Tm, double* Gm, double* scr) {
+// Gm (kk x kk) receives V^T V; scr holds kk*kk doubles.  With `pad` (shared,
+// MAXW * HT_NB_MAX doubles) the Gram product reads a copy of Vs with the odd
+// leading dimension w + 1 when it fits, so that the lanes (consecutive
+// columns a) hit distinct banks.
+__device__ void form_t_rec(int kk, double* Tm, const double* Gm, double* scr);
+__device__ void form_t(const double* Vs, const double* tau, int w, int kk, double* Tm, double* Gm, double* scr,
+                       double* pad = nullptr) {
   const int tid = threadIdx.x;
+  const bool use_pad = pad && (w + 1) * kk <= MAXW * HT_NB_MAX;
+  const int wp = use_pad ? w + 1 : w;
+  const double* Vg = use_pad ? pad : Vs;
+  if (use_pad) {
+    for (int e = tid; e < w * kk; e += blockDim.x) pad[(e % w) + (e / w) * wp] = Vs[e];
+    __syncthreads();
+  }
   for (int e = tid; e < kk * kk; e += blockDim.x) {
     const int a = e % kk, b = e / kk;
     Tm[e] = (a == b) ? tau[a] : 0.0;
@@ -153,14 +187,21 @@ __device__ void form_t(const double* Vs, const double* tau, int w, int kk, doubl
     if (a < b) {
       int r = 0;
       for (; r + 1 < w; r += 2) {
-        d0 += Vs[r + a * w] * Vs[r + b * w];
-        d1 += Vs[r + 1 + a * w] * Vs[r + 1 + b * w];
+        d0 += Vg[r + a * wp] * Vg[r + b * wp];
+        d1 += Vg[r + 1 + a * wp] * Vg[r + 1 + b * wp];
       }
-      if (r < w) d0 += Vs[r + a * w] * Vs[r + b * w];
+      if (r < w) d0 += Vg[r + a * wp] * Vg[r + b * wp];
     }
     Gm[e] = d0 + d1;
   }
   __syncthreads();
+  form_t_rec(kk, Tm, Gm, scr);
+}
+
+// The recursion of form_t on a given Gram matrix (strict upper triangle of
+// Gm) and a Tm that holds diag(tau) with zeros elsewhere.
+__device__ void form_t_rec(int kk, double* Tm, const double* Gm, double* scr) {
+  const int tid = threadIdx.x;
   for (int h = 1; h < kk; h *= 2) {
     // pairs (lo block [p0, p0+h), hi block [p0+h, p0+2h)): T12 = -T11 (G12 T22)
     for (int e = tid; e < kk * kk; e += blockDim.x) {
@@ -279,7 +320,7 @@ __global__ void __launch_bounds__(HT_THREADS) form_wy_kernel(double* wyR, double
   for (int e = threadIdx.x; e < w * k; e += blockDim.x) f.Vs[e] = Vw[e];
   for (int q = threadIdx.x; q < k; q += blockDim.x) f.tau[q] = Ww[q];
   __syncthreads();
-  form_t(f.Vs, f.tau, w, k, f.Tm, f.Gm, f.scr);
+  form_t(f.Vs, f.tau, w, k, f.Tm, f.Gm, f.scr, f.X);
   form_w(f.Vs, f.Tm, w, k, Ww);
 }
 
@@ -477,23 +518,31 @@ __global__ void __launch_bounds__(HT_THREADS, 1) restore_kernel(RestoreArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Restore chains with the application overlapped (grids of >= 6 CTAs).  The
-// step-t transform G_t has to reach every line on the far side of the factored
-// block (rows above for the RQ restore, columns to the right for the QR one),
-// but step t + 1 only needs it on the lines of the next block.  So one grid
-// barrier per step:
-//   phase 1 (iteration t): CTA 0 factors step t (after the helpers have
-//           brought the next block up to date, see phase 2) and forms T_t;
-//           CTA 1 forms Ww_{t-1}; CTAs 2.. apply G_{t-1} to the lines beyond
-//           step t-1's next block;
-//   grid barrier;
-//   phase 2: CTAs 2..5 apply G_t to the next block (8 lines each) and count
-//           (hcount); CTA 0 starts the next factorization when all four have.
-// Each line still takes G_0, G_1, ... in order: the lines beyond a next block
-// get G_{t-1} in phase 1 of iteration t and the block that becomes next at
-// step t gets G_t only after that phase's barrier.
+// Restore chains as a stream of reflectors (grids of >= 19 CTAs).  The step-t
+// transform G_t must reach every line on the far side of the factored block
+// (rows above for the RQ restore, columns to the right for the QR one), each
+// line taking G_0, G_1, ... in order, but step t + 1 only needs it on the
+// lines of the next block.  One grid barrier per step; in iteration t:
+//   CTA 0   factors step t and publishes every reflector the moment it is
+//           formed (V_t column, tau, then a release flag: t * RS_KSTEP + q + 1);
+//   CTAs 2..17 (helpers) hold the lines of step t's next block in registers,
+//           one line per warp, apply G_{t-1} and then G_t reflector by
+//           reflector as the flags arrive, so the next block is up to date
+//           when the factorization ends;
+//   CTA 1   first finishes T_{t-1} (the recursion on the Gram matrix it built
+//           in the previous iteration), raises tflag, then builds the Gram
+//           columns of step t as the reflectors arrive; CTA 18 forms Ww_{t-1};
+//   others  apply G_{t-1} with T_{t-1} (after tflag) to the lines beyond step
+//           t's next block.
+// The step time is the factorization alone.  A helper's wait is bounded; on a
+// timeout it raises HT_ERR_TIMEOUT and stops, and every CTA keeps joining the
+// barriers.
 // ---------------------------------------------------------------------------
-constexpr int RS_HELP = 4;
+constexpr int RS_HELP = 16;                   // helper CTAs (two lines each for k = 32)
+constexpr int RS_WCTA = 2 + RS_HELP;          // forms Ww of the previous step
+constexpr int RS_FIRST_BULK = RS_WCTA + 1;
+constexpr int RS_THREADS = HT_THREADS + 32;   // a ninth warp publishes the reflectors
+constexpr int RS_KSTEP = 2 * HT_NB_MAX;       // flag values per step (> reflectors per step)
 
 struct SplitArgs {
   int mode, p, k, j, n;
@@ -502,8 +551,9 @@ struct SplitArgs {
   double* wy;
   size_t stride;
   double* tstore;
-  int* hcount;  // helper completions (zeroed by the launcher)
-  int* err;     // device error word (HT_ERR_TIMEOUT if the wait for the helpers gave up)
+  double* taus;  // tau of step t at taus + t * k
+  int* flag;     // [0] reflectors published, [1] T factors formed (zeroed by the launcher)
+  int* err;      // device error word
   unsigned long long* ptime;
 };
 
@@ -532,98 +582,278 @@ __device__ __forceinline__ SplitStep split_step(bool right, int p, int k, int s)
   return g;
 }
 
-__global__ void __launch_bounds__(HT_THREADS, 1) restore_split_kernel(SplitArgs a) {
+// bounded wait of one thread for *p >= v; raises HT_ERR_TIMEOUT on expiry
+__device__ bool split_wait(const int* p, int v, int* err) {
+  if (ht_ld_acquire(p) >= v) return true;
+  for (long it = 0; it < (long)HT_SPIN_LIMIT; ++it) {
+    __nanosleep(32);
+    if (ht_ld_acquire(p) >= v) return true;
+  }
+  atomicCAS(err, 0, HT_ERR_TIMEOUT);
+  return false;
+}
+
+// The reflectors of one step (V at gV, ld w; tau at gTau; QL pattern for
+// right, QR for left; kk of them in product order) applied to one line held in
+// registers by one warp (at most four rows per lane, w <= 128), reflector q
+// once flag >= base + q + 1 (SMEM: V and tau already in shared memory, every
+// reflector published, no waiting).  Returns false on a timeout.
+template <bool SMEM>
+__device__ bool split_reflect(bool right, double x[4], int w, int kk, const double* gV, const double* gTau,
+                              const int* flag, int base, int* err) {
+  const int lane = threadIdx.x & 31;
+  // reflector data: tau and v issued together; while this warp is behind the
+  // factorization (the next flag already up) the next reflector is fetched
+  // before the current one is applied
+  auto fetch = [&](int q, double v[4], double& beta) {
+    beta = SMEM ? gTau[q] : __ldcg(gTau + q);
+    const int lo = right ? 0 : q, hi = right ? w - q : w;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = lane + 32 * u;
+      v[u] = (r >= lo && r < hi) ? (SMEM ? gV[r + q * w] : __ldcg(gV + r + (size_t)q * w)) : 0.0;
+    }
+  };
+  auto ready = [&](int q, bool wait) -> int {  // 1: published, 0: not yet, -1: timeout
+    int st = 1;
+    if (!SMEM && lane == 0) {
+      if (wait) st = split_wait(flag, base + q + 1, err) ? 1 : -1;
+      else st = (ht_ld_acquire(flag) >= base + q + 1) ? 1 : 0;
+    }
+    return __shfl_sync(0xffffffffu, st, 0);
+  };
+  double v[4], beta = 0.0;
+  if (kk <= 0) return true;
+  if (ready(0, true) < 0) return false;
+  fetch(0, v, beta);
+  for (int q = 0; q < kk; ++q) {
+    double vn[4] = {0.0, 0.0, 0.0, 0.0}, bn = 0.0;
+    int nxt = 0;
+    if (q + 1 < kk) {
+      nxt = ready(q + 1, false);
+      if (nxt > 0) fetch(q + 1, vn, bn);
+    }
+    if (beta != 0.0) {
+      double d = 0.0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) d += v[u] * x[u];
+      d = beta * ht_warp_sum(d);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) x[u] -= d * v[u];
+    }
+    if (q + 1 < kk) {
+      if (nxt == 0) {
+        if (ready(q + 1, true) < 0) return false;
+        fetch(q + 1, vn, bn);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = vn[u];
+      beta = bn;
+    }
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(RS_THREADS, 1) restore_split_kernel(SplitArgs a) {
   cg::grid_group grid = cg::this_grid();
   extern __shared__ double sm[];
-  __shared__ int ok;
   FSm f = fsm(sm);
-  double* Xs = f.Tm;  // stripe buffers reuse Tm, Gm, scr
+  double* Xs = f.Tm;  // stripe buffers of the bulk reuse Tm, Gm, scr
   double* Ps = Xs + SRR * MAXW;
   double* P2 = Ps + SRR * HT_NB_MAX;
   const int p = a.p, k = a.k, j1 = a.j + 1;
   const bool right = (a.mode == 2);
   const int nsteps = right ? ht_num_right_blocks(p, k) - 1 : ht_num_left_blocks(p, k);
-  const int cta = blockIdx.x, tid = threadIdx.x;
-  bool failed = false;  // CTA 0 only: a timed-out wait; it keeps joining the barriers
+  const int cta = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  double* Bt = a.B + (size_t)j1 + (size_t)j1 * a.ldb;
   for (int t = 0; t <= nsteps; ++t) {
-    // ---- phase 1 ----
-    if (cta == 0 && t < nsteps) {
-      if (t > 0 && !failed) {
-        if (tid == 0) {
-          const unsigned long long tw = a.ptime ? rs_now() : 0ull;
-          ok = 1;
-          if (ht_ld_acquire(a.hcount) < RS_HELP * t) {
-            ok = 0;
-            for (long it = 0; it < (long)HT_SPIN_LIMIT; ++it) {
-              __nanosleep(64);
-              if (ht_ld_acquire(a.hcount) >= RS_HELP * t) { ok = 1; break; }
-            }
-            if (!ok) atomicCAS(a.err, 0, HT_ERR_TIMEOUT);
-          }
-          if (a.ptime) a.ptime[18] += rs_now() - tw;
-        }
-        __syncthreads();
-        failed = !ok;
-      }
-      if (!failed) {
+    if (cta == 0) {
+      // ---- factorization of step t, reflectors published as they form ----
+      if (t < nsteps) {
         const SplitStep g = split_step(right, p, k, t);
         const int w = g.width, kr = g.kr;
-        double* blk = right ? a.B + (size_t)(j1 + g.f0) + (size_t)(j1 + g.off) * a.ldb
-                            : a.B + (size_t)(j1 + g.off) + (size_t)(j1 + g.off) * a.ldb;
         for (int e = tid; e < w * kr; e += blockDim.x) {
           const int r = e % w, c = e / w;
-          f.X[e] = right ? __ldcg(blk + (size_t)c + (size_t)r * a.ldb) : __ldcg(blk + (size_t)r + (size_t)c * a.ldb);
+          f.X[e] = __ldcg(right ? Bt + (size_t)(g.f0 + c) + (size_t)(g.off + r) * a.ldb
+                                : Bt + (size_t)(g.off + r) + (size_t)(g.f0 + c) * a.ldb);
         }
         __syncthreads();
         const unsigned long long t0 = (a.ptime && tid == 0) ? rs_now() : 0ull;
-        house_factor(f.X, w, kr, right, f.Vs, f.tau, f.nrm, f.bv);
-        const unsigned long long t1 = (a.ptime && tid == 0) ? rs_now() : 0ull;
-        form_t(f.Vs, f.tau, w, kr, f.Tm, f.Gm, f.scr);
-        if (a.ptime && tid == 0) {
-          const unsigned long long t2 = rs_now();
-          a.ptime[16] += t1 - t0;
-          a.ptime[17] += t2 - t1;
-        }
-        double* Vw = a.wy + (size_t)t * a.stride;
-        double* Tg = a.tstore + (size_t)t * k * k;
+        const HousePub pub{a.wy + (size_t)t * a.stride, a.taus + (size_t)t * k, a.flag, t * RS_KSTEP};
+        house_factor(f.X, w, kr, right, f.Vs, f.tau, f.nrm, f.bv, &pub);
+        if (a.ptime && tid == 0) a.ptime[16] += rs_now() - t0;
         for (int e = tid; e < w * kr; e += blockDim.x) {
           const int r = e % w, c = e / w;
-          if (right) blk[(size_t)c + (size_t)r * a.ldb] = f.X[e];
-          else blk[(size_t)r + (size_t)c * a.ldb] = f.X[e];
-          Vw[e] = f.Vs[e];
+          *(right ? Bt + (size_t)(g.f0 + c) + (size_t)(g.off + r) * a.ldb
+                  : Bt + (size_t)(g.off + r) + (size_t)(g.f0 + c) * a.ldb) = f.X[e];
         }
+      }
+    } else if (cta == 1) {
+      const unsigned long long t0 = (a.ptime && tid == 0) ? rs_now() : 0ull;
+      if (t > 0) {
+        // T_{t-1} from the Gram matrix, tau and V of step t-1 kept in shared memory, then Ww_{t-1}
+        const SplitStep g = split_step(right, p, k, t - 1);
+        const int kr = g.kr;
+        for (int e = tid; e < kr * kr; e += blockDim.x) f.Tm[e] = (e % kr == e / kr) ? f.tau[e % kr] : 0.0;
+        __syncthreads();
+        form_t_rec(kr, f.Tm, f.Gm, f.scr);
+        double* Tg = a.tstore + (size_t)(t - 1) * k * k;
         for (int e = tid; e < kr * kr; e += blockDim.x) Tg[e] = f.Tm[e];
         __threadfence();
+        __syncthreads();
+        if (tid == 0) ht_st_release(a.flag + 1, t);
       }
-    } else if (cta == 1 && t > 0) {
-      // Ww = Vw T^T of step t - 1 for the later sweeps
-      const SplitStep g = split_step(right, p, k, t - 1);
-      const double* Vw = a.wy + (size_t)(t - 1) * a.stride;
-      const double* Tg = a.tstore + (size_t)(t - 1) * k * k;
-      for (int e = tid; e < g.width * g.kr; e += blockDim.x) f.Vs[e] = __ldcg(Vw + e);
-      for (int e = tid; e < g.kr * g.kr; e += blockDim.x) f.Tm[e] = __ldcg(Tg + e);
-      __syncthreads();
-      form_w(f.Vs, f.Tm, g.width, g.kr, a.wy + (size_t)(t - 1) * a.stride + a.stride / 2);
-    } else if (cta >= 2 && t > 0) {
-      // G_{t-1} to the lines beyond step t-1's next block
-      const SplitStep g = split_step(right, p, k, t - 1);
-      const unsigned long long t0 = (a.ptime && cta == 2 && tid == 0) ? rs_now() : 0ull;
-      apply_vt(right, a.B, a.ldb, j1 + g.b0, j1 + g.b1, j1 + g.off, g.width, g.kr, a.wy + (size_t)(t - 1) * a.stride,
-               a.tstore + (size_t)(t - 1) * k * k, Xs, Ps, P2, f.Vs, f.Gm, cta - 2, (int)gridDim.x - 2);
-      if (a.ptime && cta == 2 && tid == 0) a.ptime[19] += rs_now() - t0;
+      if (t < nsteps) {
+        // Gram columns of step t as the reflectors arrive
+        const SplitStep g = split_step(right, p, k, t);
+        const int w = g.width, kr = g.kr, nw = blockDim.x >> 5;
+        const double* gV = a.wy + (size_t)t * a.stride;
+        for (int q = 0; q < kr; ++q) {
+          __shared__ int okb;
+          if (tid == 0) okb = split_wait(a.flag, t * RS_KSTEP + q + 1, a.err);
+          __syncthreads();
+          if (!okb) break;
+          for (int r = tid; r < w; r += blockDim.x) f.Vs[r + q * w] = __ldcg(gV + r + (size_t)q * w);
+          if (tid == 0) f.tau[q] = __ldcg(a.taus + (size_t)t * k + q);
+          __syncthreads();
+          for (int c = wid; c < q; c += nw) {
+            double d = 0.0;
+            for (int r = lane; r < w; r += 32) d += f.Vs[r + c * w] * f.Vs[r + q * w];
+            d = ht_warp_sum(d);
+            if (lane == 0) f.Gm[c + q * kr] = d;
+          }
+        }
+        __syncthreads();
+      }
+      if (a.ptime && tid == 0) a.ptime[17] += rs_now() - t0;
+    } else if (cta < 2 + RS_HELP) {
+      // ---- helpers: the next block of step t takes G_{t-1}, then G_t as it streams ----
+      if (t < nsteps) {
+        const unsigned long long t0 = (a.ptime && cta == 2 && tid == 0) ? rs_now() : 0ull;
+        const SplitStep g = split_step(right, p, k, t);
+        const int nl = g.n1 - g.n0, per = (nl + RS_HELP - 1) / RS_HELP;
+        const int l0 = g.n0 + (cta - 2) * per, l1 = min(g.n1, l0 + per);
+        const SplitStep gp = split_step(right, p, k, t > 0 ? t - 1 : 0);
+        if (t > 0 && l1 > l0) {
+          // the reflectors of step t-1 (all published) from shared memory
+          const double* Vp = a.wy + (size_t)(t - 1) * a.stride;
+          for (int e = tid; e < gp.width * gp.kr; e += blockDim.x) f.Vs[e] = __ldcg(Vp + e);
+          for (int q = tid; q < gp.kr; q += blockDim.x) f.tau[q] = __ldcg(a.taus + (size_t)(t - 1) * k + q);
+          __syncthreads();
+        }
+        for (int line = l0 + wid; line < l1; line += blockDim.x >> 5) {
+          double x[4];
+          // the line over the union of both windows: right [off_t, off_t + width_t) holds both
+          // transforms' columns (step t-1 acts on [off_{t-1}, ...) which is inside); left likewise
+          const int lo = min(g.off, gp.off), hi = max(g.off + g.width, gp.off + gp.width);
+          const int wu = (t > 0) ? hi - lo : g.width, ou = (t > 0) ? lo : g.off;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int r = lane + 32 * u;
+            x[u] = (r < wu) ? __ldcg(right ? Bt + (size_t)line + (size_t)(ou + r) * a.ldb
+                                           : Bt + (size_t)(ou + r) + (size_t)line * a.ldb)
+                            : 0.0;
+          }
+          bool ok = true;
+          if (t > 0) {
+            // G_{t-1} acts on rows [gp.off - ou, ...) of x: shift into its own frame
+            double y[4];
+            const int sh = gp.off - ou;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int r = lane + 32 * u;  // row of the window of step t-1
+              const int src = r + sh;
+              y[u] = 0.0;
+#pragma unroll
+              for (int v2 = 0; v2 < 4; ++v2) {
+                const double xv = __shfl_sync(0xffffffffu, x[v2], src & 31);
+                if ((src >> 5) == v2 && src < wu) y[u] = xv;
+              }
+            }
+            ok = split_reflect<true>(right, y, gp.width, gp.kr, f.Vs, f.tau, a.flag, (t - 1) * RS_KSTEP, a.err);
+            // back into the union frame
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int r = lane + 32 * u;  // row of the union
+              const int src = r - sh;       // row of step t-1's window
+#pragma unroll
+              for (int v2 = 0; v2 < 4; ++v2) {
+                const double yv = __shfl_sync(0xffffffffu, y[v2], src & 31);
+                if (src >= 0 && src < gp.width && (src >> 5) == v2) x[u] = yv;
+              }
+            }
+          }
+          if (ok) {
+            double y[4];
+            const int sh = g.off - ou;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int r = lane + 32 * u;
+              const int src = r + sh;
+              y[u] = 0.0;
+#pragma unroll
+              for (int v2 = 0; v2 < 4; ++v2) {
+                const double xv = __shfl_sync(0xffffffffu, x[v2], src & 31);
+                if ((src >> 5) == v2 && src < wu) y[u] = xv;
+              }
+            }
+            ok = split_reflect<false>(right, y, g.width, g.kr, a.wy + (size_t)t * a.stride, a.taus + (size_t)t * k, a.flag,
+                                      t * RS_KSTEP, a.err);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int r = lane + 32 * u;
+              const int src = r - sh;
+#pragma unroll
+              for (int v2 = 0; v2 < 4; ++v2) {
+                const double yv = __shfl_sync(0xffffffffu, y[v2], src & 31);
+                if (src >= 0 && src < g.width && (src >> 5) == v2) x[u] = yv;
+              }
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int r = lane + 32 * u;
+            if (r < wu) *(right ? Bt + (size_t)line + (size_t)(ou + r) * a.ldb : Bt + (size_t)(ou + r) + (size_t)line * a.ldb) = x[u];
+          }
+        }
+        if (a.ptime && cta == 2 && tid == 0) a.ptime[18] += rs_now() - t0;
+      }
+    } else if (cta == RS_WCTA) {
+      if (t > 0) {
+        // Ww_{t-1} = V T^T for the later sweeps, once T_{t-1} is formed
+        const SplitStep g = split_step(right, p, k, t - 1);
+        if (tid == 0) split_wait(a.flag + 1, t, a.err);
+        __syncthreads();
+        const double* Vw = a.wy + (size_t)(t - 1) * a.stride;
+        const double* Tg = a.tstore + (size_t)(t - 1) * k * k;
+        for (int e = tid; e < g.width * g.kr; e += blockDim.x) f.Vs[e] = __ldcg(Vw + e);
+        for (int e = tid; e < g.kr * g.kr; e += blockDim.x) f.Tm[e] = __ldcg(Tg + e);
+        __syncthreads();
+        form_w(f.Vs, f.Tm, g.width, g.kr, a.wy + (size_t)(t - 1) * a.stride + a.stride / 2);
+      }
+    } else if (t > 0) {
+      // ---- bulk: G_{t-1} with T_{t-1} beyond step t's next block (step t-1's at the end) ----
+      const SplitStep gp = split_step(right, p, k, t - 1);
+      int b0, b1;
+      if (t < nsteps) {
+        const SplitStep g = split_step(right, p, k, t);
+        b0 = g.b0; b1 = g.b1;
+      } else {
+        b0 = gp.b0; b1 = gp.b1;
+      }
+      if (b1 > b0 && cta - RS_FIRST_BULK < (b1 - b0 + SRR - 1) / SRR) {
+        if (tid == 0) split_wait(a.flag + 1, t, a.err);  // T_{t-1} formed (a timeout is reported, work goes on)
+        __syncthreads();
+      }
+      const unsigned long long t0 = (a.ptime && cta == RS_FIRST_BULK && tid == 0) ? rs_now() : 0ull;
+      apply_vt(right, a.B, a.ldb, j1 + b0, j1 + b1, j1 + gp.off, gp.width, gp.kr, a.wy + (size_t)(t - 1) * a.stride,
+               a.tstore + (size_t)(t - 1) * k * k, Xs, Ps, P2, f.Vs, f.Gm, cta - RS_FIRST_BULK,
+               (int)gridDim.x - RS_FIRST_BULK);
+      if (a.ptime && cta == RS_FIRST_BULK && tid == 0) a.ptime[19] += rs_now() - t0;
     }
     if (t == nsteps) break;
+    __threadfence();
     grid.sync();
-    // ---- phase 2: G_t to the next block ----
-    if (cta >= 2 && cta < 2 + RS_HELP) {
-      const SplitStep g = split_step(right, p, k, t);
-      if (g.n1 > g.n0)
-        apply_vt(right, a.B, a.ldb, j1 + g.n0, j1 + g.n1, j1 + g.off, g.width, g.kr, a.wy + (size_t)t * a.stride,
-                 a.tstore + (size_t)t * k * k, Xs, Ps, P2, f.Vs, f.Gm, cta - 2, RS_HELP);
-      __threadfence();
-      __syncthreads();
-      if (tid == 0) atomicAdd(a.hcount, 1);
-    }
   }
 }
 
@@ -653,19 +883,20 @@ cudaError_t ht_launch_chains(cudaStream_t st, double* V2, double* U2, long ld, i
 }
 
 cudaError_t ht_launch_restore(cudaStream_t st, int mode, int p, int k, int j, int n, double* B, long ldb, double* wy,
-                              size_t stride, double* tstore, int* hcount, int* err, unsigned long long* ptime) {
+                              size_t stride, double* tstore, double* taus, int* flag, int* err,
+                              unsigned long long* ptime) {
   set_factor_attr();
   const int nsteps = (mode == 2) ? ht_num_right_blocks(p, k) - 1 : ht_num_left_blocks(p, k);
   if (nsteps <= 0) return cudaSuccess;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (sms >= 2 + RS_HELP && hcount && err) {
-    cudaError_t e = cudaMemsetAsync(hcount, 0, sizeof(int), st);
+  if (k <= 32 && sms > RS_FIRST_BULK && flag && err && taus) {  // the helpers hold three blocks of a line
+    cudaError_t e = cudaMemsetAsync(flag, 0, 2 * sizeof(int), st);
     if (e != cudaSuccess) return e;
-    SplitArgs sa{mode, p, k, j, n, B, ldb, wy, stride, tstore, hcount, err, ptime};
+    SplitArgs sa{mode, p, k, j, n, B, ldb, wy, stride, tstore, taus, flag, err, ptime};
     void* sargs[] = {&sa};
-    return cudaLaunchCooperativeKernel((void*)restore_split_kernel, dim3(sms), dim3(HT_THREADS), sargs,
+    return cudaLaunchCooperativeKernel((void*)restore_split_kernel, dim3(sms), dim3(RS_THREADS), sargs,
                                        factor_smem_doubles() * sizeof(double), st);
   }
   RestoreArgs a{mode, p, k, j, n, B, ldb, wy, stride, tstore, ptime};

@@ -153,25 +153,27 @@ __device__ void tile_gemv(const double* M, long ld, int r0, int rows, int c0, in
 // Row tile of a GEMV streamed from memory: returns, to thread r < rows (<= 32),
 // sum_c M(r0 + r, c0 + c) x[c] over c < cols.  Lanes take rows (coalesced:
 // consecutive rows of a column are contiguous), the warps take interleaved
-// columns, eight columns per step so that eight loads per thread are in
-// flight; x is read from global memory (XG, every lane the same address) or
+// columns, GU columns per step so that GU loads per thread are in flight
+// (with one CTA per SM, 16 x 8 B x 256 threads keeps ~32 KB per SM in flight,
+// about what HBM latency x bandwidth per SM asks for); x is read from global memory (XG, every lane the same address) or
 // shared memory.  red: blockDim.x doubles of shared scratch.  Two barriers.
+constexpr int GU = 16;
 template <bool XG>
 __device__ double gemv32(const double* M, long ld, int r0, int rows, int c0, int cols, const double* x, double* red) {
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double a0 = 0.0, a1 = 0.0;
   if (lane < rows) {
     const double* p = M + (size_t)(r0 + lane) + (size_t)c0 * ld;
-    for (int c = wi; c < cols; c += 8 * nw) {
-      double mv[8], xv[8];
+    for (int c = wi; c < cols; c += GU * nw) {
+      double mv[GU], xv[GU];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < GU; ++u) {
         const int cc = c + u * nw;
         mv[u] = (cc < cols) ? __ldcg(p + (size_t)cc * ld) : 0.0;
         xv[u] = (cc < cols) ? (XG ? __ldcg(x + cc) : x[cc]) : 0.0;
       }
 #pragma unroll
-      for (int u = 0; u < 8; u += 2) {
+      for (int u = 0; u < GU; u += 2) {
         a0 += mv[u] * xv[u];
         a1 += mv[u + 1] * xv[u + 1];
       }
