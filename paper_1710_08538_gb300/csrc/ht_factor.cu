@@ -704,23 +704,66 @@ __global__ void __launch_bounds__(RS_THREADS, 1) restore_split_kernel(SplitArgs 
         if (tid == 0) ht_st_release(a.flag + 1, t);
       }
       if (t < nsteps) {
-        // Gram columns of step t as the reflectors arrive
+        // Gram columns of step t as the reflectors arrive, without block barriers:
+        // warp wi keeps the columns c = wi (mod nw) in shared memory and, for every
+        // arriving v_q (fetched by each warp itself, the next one early when its
+        // flag is already up), forms Gm(c, q) for its c < q
         const SplitStep g = split_step(right, p, k, t);
         const int w = g.width, kr = g.kr, nw = blockDim.x >> 5;
         const double* gV = a.wy + (size_t)t * a.stride;
-        for (int q = 0; q < kr; ++q) {
-          __shared__ int okb;
-          if (tid == 0) okb = split_wait(a.flag, t * RS_KSTEP + q + 1, a.err);
-          __syncthreads();
-          if (!okb) break;
-          for (int r = tid; r < w; r += blockDim.x) f.Vs[r + q * w] = __ldcg(gV + r + (size_t)q * w);
-          if (tid == 0) f.tau[q] = __ldcg(a.taus + (size_t)t * k + q);
-          __syncthreads();
+        const double* gT = a.taus + (size_t)t * k;
+        const int base = t * RS_KSTEP;
+        auto ready = [&](int q, bool wait) -> int {
+          int st = 0;
+          if (lane == 0) {
+            if (wait) st = split_wait(a.flag, base + q + 1, a.err) ? 1 : -1;
+            else st = (ht_ld_acquire(a.flag) >= base + q + 1) ? 1 : 0;
+          }
+          return __shfl_sync(0xffffffffu, st, 0);
+        };
+        double v[4];
+        auto fetch = [&](int q, double* dst) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int r = lane + 32 * u;
+            dst[u] = (r < w) ? __ldcg(gV + r + (size_t)q * w) : 0.0;
+          }
+        };
+        bool okw = ready(0, true) > 0;
+        if (okw) fetch(0, v);
+        for (int q = 0; q < kr && okw; ++q) {
+          double vn[4] = {0.0, 0.0, 0.0, 0.0};
+          int nxt = 0;
+          if (q + 1 < kr) {
+            nxt = ready(q + 1, false);
+            if (nxt > 0) fetch(q + 1, vn);
+          }
           for (int c = wid; c < q; c += nw) {
             double d = 0.0;
-            for (int r = lane; r < w; r += 32) d += f.Vs[r + c * w] * f.Vs[r + q * w];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int r = lane + 32 * u;
+              if (r < w) d += f.Vs[r + c * w] * v[u];
+            }
             d = ht_warp_sum(d);
             if (lane == 0) f.Gm[c + q * kr] = d;
+          }
+          if (q % nw == wid) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int r = lane + 32 * u;
+              if (r < w) f.Vs[r + q * w] = v[u];
+            }
+            if (lane == 0) f.tau[q] = __ldcg(gT + q);
+            __syncwarp();
+          }
+          if (q + 1 < kr) {
+            if (nxt == 0) {
+              okw = ready(q + 1, true) > 0;
+              if (okw) fetch(q + 1, vn);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = vn[u];
           }
         }
         __syncthreads();
