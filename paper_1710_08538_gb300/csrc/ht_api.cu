@@ -80,9 +80,10 @@ size_t ht_layout_work(HtWork& w, char* b, int n, int nb, int G, unsigned long lo
   const int nbi = (n + HT_TRSV_BI - 1) / HT_TRSV_BI + 1;
   const size_t oXinv = take((size_t)nbi * HT_TRSV_BI * HT_TRSV_BI);
   const size_t oSafe = take((size_t)nbi);
-  const size_t oXmax = take(256);
+  const size_t oXmax = take((size_t)32 * nbi + 256);
+  const size_t oProg = take((size_t)G), oNear = take(HT_TRSV_BI);
   const size_t oTst = take(nn * nb + 4 * (size_t)nb * nb);  // (p/k + 1) T factors of k^2 each
-  const size_t oWpart = take((size_t)((n + 4 * HT_TRSV_BS - 1) / (4 * HT_TRSV_BS) + 1) * nn);
+  const size_t oWpart = take((size_t)((n + HT_TRMV_CW - 1) / HT_TRMV_CW + 1) * nn);
   // digits of the emulated sweeps: windows of a chain are processed in launches of emu_cap windows
   const size_t emu_win = nb <= 32 ? ht_emu_window_bytes(nb) : 0;
   w.emu_cap = std::min(n / 32 + 4, 1024);
@@ -117,6 +118,8 @@ size_t ht_layout_work(HtWork& w, char* b, int n, int nb, int G, unsigned long lo
   w.Xinv = (double*)(b + oXinv);
   w.safe = (int*)(b + oSafe);
   w.xmax = (double*)(b + oXmax);
+  w.prog = (unsigned long long*)(b + oProg);
+  w.nearv = (double*)(b + oNear);
   w.emu_dig = emu_win ? (void*)(b + oEmu) : nullptr;
   w.emu_exps = (int*)(b + oEmuE);
   w.rcount = (int*)(b + oRc);

@@ -17,6 +17,7 @@
 
 #define HT_THREADS 256
 #define HT_TRSV_BS 64          // row tile of the triangular solve / multiply
+#define HT_TRMV_CW 1024        // column chunk of the triangular multiply B w (partials per chunk)
 #define HT_TRSV_BI 256         // diagonal block of the grid-synchronous solve (explicit inverses)
 #define HT_NB_MAX 64           // largest panel width (windows live in shared memory)
 #define HT_BIG_EXP 500         // rescale threshold 2^500 of the scaled solve
@@ -126,7 +127,9 @@ struct HtWork {
   unsigned long long* ptime;  // per-phase panel timers (profile mode) or null
   double* Xinv;            // inverses of the diagonal blocks of the trailing B (n x HT_TRSV_BI)
   int* safe;               // per diagonal block: inverse usable
-  double* xmax;            // per-CTA max |x| partials
+  double* xmax;            // per diagonal block of the solve: 32 partial max |x| slots
+  unsigned long long* prog;  // solve progress word per panel CTA (epoch-stamped, look-ahead solve)
+  double* nearv;           // update of the next diagonal block of the solve (HT_TRSV_BI)
   double* wpart;           // chunk partials of the triangular multiply
   double* tstore;          // T factors of the restore steps (HT_NB_MAX^2 each)
   int* rcount;             // restore: reflectors published (a step-stamped counter)
@@ -254,5 +257,13 @@ __device__ __forceinline__ int ht_ld_acquire(const int* p) {
 }
 __device__ __forceinline__ void ht_st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ht_ld_acquire64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void ht_st_release64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 #endif

@@ -14,8 +14,10 @@
 //        Y = A V T (Sec. 3.2.2d); rows 0..s of Y are formed later (Remark 3.1).
 // The FP64 work of a column is two passes over the triangle of B (solve,
 // residual) and one over A(s+1:n, j+1:n) (the Y column): HBM- and
-// DFMA-bound; the triangular solve is a wavefront over 64-row blocks that
-// CTAs publish through flags (bounded spins, error word on timeout).
+// DFMA-bound.  The triangular solve works on 256-row diagonal blocks with
+// precomputed inverses: a chain of 32 CTAs solves block after block while the
+// other CTAs apply each solved block to the rows above, one step behind,
+// synchronised through progress words (bounded spins, error word on timeout).
 #include <cooperative_groups.h>
 
 #include "ht_common.cuh"
@@ -51,7 +53,9 @@ struct PanelArgs {
   unsigned long long* ptime;  // optional per-phase nanoseconds (CTA 0), 16 slots
   double* Xinv;    // inverses of the BI x BI diagonal blocks of the trailing B (row-major, per block)
   int* safe;       // per block: 1 = solve with the inverse, 0 = scaled substitution
-  double* xmax;    // per-CTA partial max |x| of the current block (GS solve)
+  double* xmax;    // per diagonal block: 32 partial max |x| slots
+  unsigned long long* prog;  // per-CTA progress words of the look-ahead solve
+  double* nearv;   // B(block i-1, block i) x_i of the look-ahead solve
   double* wpart;   // chunk partials of the triangular multiply (nchunks x n)
 };
 
@@ -164,19 +168,33 @@ __device__ double gemv32(const double* M, long ld, int r0, int rows, int c0, int
   double a0 = 0.0, a1 = 0.0;
   if (lane < rows) {
     const double* p = M + (size_t)(r0 + lane) + (size_t)c0 * ld;
+    // two batches of matrix loads in flight: the next batch is issued before
+    // the current one is consumed; x (a broadcast, cache-resident) is read at
+    // use
+    double mv[GU];
+#pragma unroll
+    for (int u = 0; u < GU; ++u) {
+      const int cc = wi + u * nw;
+      mv[u] = (cc < cols) ? __ldcg(p + (size_t)cc * ld) : 0.0;
+    }
     for (int c = wi; c < cols; c += GU * nw) {
-      double mv[GU], xv[GU];
+      const int cn = c + GU * nw;
+      double mn[GU];
 #pragma unroll
       for (int u = 0; u < GU; ++u) {
-        const int cc = c + u * nw;
-        mv[u] = (cc < cols) ? __ldcg(p + (size_t)cc * ld) : 0.0;
-        xv[u] = (cc < cols) ? (XG ? __ldcg(x + cc) : x[cc]) : 0.0;
+        const int cc = cn + u * nw;
+        mn[u] = (cc < cols) ? __ldcg(p + (size_t)cc * ld) : 0.0;
       }
 #pragma unroll
       for (int u = 0; u < GU; u += 2) {
-        a0 += mv[u] * xv[u];
-        a1 += mv[u + 1] * xv[u + 1];
+        const int c0u = c + u * nw, c1u = c0u + nw;
+        const double x0 = (c0u < cols) ? (XG ? __ldcg(x + c0u) : x[c0u]) : 0.0;
+        const double x1 = (c1u < cols) ? (XG ? __ldcg(x + c1u) : x[c1u]) : 0.0;
+        a0 += mv[u] * x0;
+        a1 += mv[u + 1] * x1;
       }
+#pragma unroll
+      for (int u = 0; u < GU; ++u) mv[u] = mn[u];
     }
   }
   red[threadIdx.x] = a0 + a1;
@@ -411,6 +429,252 @@ __device__ void trsv_gs(const PanelArgs& a, Grid& grid, int m, const double* rhs
   }
 }
 
+// Bounded wait until the cnt progress words p[idx(0..cnt-1)] are all >=
+// target (warp 0 polls with relaxed loads, all of a lane's words in flight
+// together, then one acquire fence; the block follows).  Fails at once when
+// the error word is already set (a wait elsewhere gave up), else after
+// HT_SPIN_LIMIT polls, setting HT_ERR_TIMEOUT; the caller then carries on
+// without the data.
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+template <class Idx>
+__device__ bool la_wait(const unsigned long long* p, int cnt, Idx idx, unsigned long long target, int* err) {
+  __shared__ int flag[1];
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    int ok = 0;
+    for (long it = 0; it <= (long)HT_SPIN_LIMIT; ++it) {
+      unsigned long long v[4] = {~0ull, ~0ull, ~0ull, ~0ull};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (lane + 32 * u < cnt) v[u] = ld_relaxed64(p + idx(lane + 32 * u));
+      bool mine = (v[0] >= target) && (v[1] >= target) && (v[2] >= target) && (v[3] >= target);
+      for (int c = lane + 128; c < cnt; c += 32) mine = mine && (ld_relaxed64(p + idx(c)) >= target);
+      if (__all_sync(0xffffffffu, mine)) { ok = 1; break; }
+      if (*(volatile int*)err != 0) break;
+      __nanosleep(32);
+    }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    if (!ok && lane == 0) atomicCAS(err, 0, HT_ERR_TIMEOUT);
+    if (lane == 0) *flag = ok;
+  }
+  __syncthreads();
+  const bool ok = *flag != 0;
+  __syncthreads();
+  return ok;
+}
+
+// la_wait for two groups at once: words p[0..cntA) against targetA and
+// p[idxB(0..cntB-1)] (cntB <= 32) against targetB, all loads of a poll in flight together.
+template <class IdxB>
+__device__ bool la_wait2(const unsigned long long* p, int cntA, unsigned long long targetA, int cntB, IdxB idxB,
+                         unsigned long long targetB, int* err) {
+  __shared__ int flag2[1];
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    int ok = 0;
+    for (long it = 0; it <= (long)HT_SPIN_LIMIT; ++it) {
+      const unsigned long long va = (lane < cntA) ? ld_relaxed64(p + lane) : ~0ull;
+      const unsigned long long vb = (lane < cntB) ? ld_relaxed64(p + idxB(lane)) : ~0ull;
+      if (__all_sync(0xffffffffu, va >= targetA && vb >= targetB)) { ok = 1; break; }
+      if (*(volatile int*)err != 0) break;
+      __nanosleep(32);
+    }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    if (!ok && lane == 0) atomicCAS(err, 0, HT_ERR_TIMEOUT);
+    if (lane == 0) *flag2 = ok;
+  }
+  __syncthreads();
+  const bool ok = *flag2 != 0;
+  __syncthreads();
+  return ok;
+}
+
+// Publishes this CTA's progress word after every thread's stores of the step
+// (the barrier orders them before the release store of thread 0).
+__device__ __forceinline__ void la_publish(unsigned long long* p, unsigned long long v) {
+  __syncthreads();
+  if (threadIdx.x == 0) ht_st_release64(p, v);
+}
+
+// Look-ahead blocked backward substitution B_loc y = 2^{-E} rhs: the same
+// arithmetic as trsv_gs (every sum in the same order, so the same result) on
+// a schedule without grid barriers.  CTAs [0, LA_ND) form the diagonal chain:
+// for block i they (P1) take x_i from the block inverse (or by scaled
+// substitution on CTA 0) and then (P2) the update of the next diagonal block,
+// B(block i-1, block i) x_i, into nearv.  CTAs [LA_ND, G) subtract
+// B(rows above block i-1, block i) x_i from their 32-row tiles of the
+// accumulator, running up to one step behind the chain, which needs their
+// update of step i+2 only when it reaches block i.  Progress words (release /
+// acquire, epoch-stamped, bounded waits) replace the barriers: chain CTA c
+// publishes base + 2 s + 1 after P1 and base + 2 s + 2 after P2 of step s (block
+// nbk-1-s), the other CTAs base + s + 1 after their update of step s.  Every
+// CTA follows the same frame exponent as trsv_gs from the published per-block
+// maxima (xmax, 32 slots per block) and frame shifts (flags).
+constexpr int LA_ND = 32;
+__device__ __forceinline__ void cp_async8(double* smem, const double* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+__device__ void trsv_la(const PanelArgs& a, int m, double* accv, double* sol, bool force_subst, unsigned epoch,
+                        double* tile, double* red4, double* xl, double* xs, double* red, int* shi, double* Bt) {
+  const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+  const int nbk = (m + BI - 1) / BI;
+  const double* Bl = a.B + (size_t)(a.s + 1) + (size_t)(a.s + 1) * a.ldb;
+  const long ldb = a.ldb;
+  const unsigned long long base = (unsigned long long)epoch << 14;
+  const bool chain = cta < LA_ND;
+  const int NF = G - LA_ND;
+  auto ident = [](int u) { return u; };
+  int E = 0;
+  // frame of the step that produced block i (identical in every CTA)
+  auto frame = [&](int i, int& sh_acc, int& sh_x) {
+    const bool sf = !force_subst && __ldcg(a.safe + i);
+    const int nparts = sf ? LA_ND : 1;
+    const int delta = __ldcg(a.flags + i);
+    if (tid < 32) {
+      const double t = ht_warp_max((tid < nparts) ? __ldcg(a.xmax + (size_t)i * 32 + tid) : 0.0);
+      if (tid == 0) red[0] = t;
+    }
+    __syncthreads();
+    const double M = red[0];
+    __syncthreads();
+    const int Ei = E + delta;
+    int En = max(E, Ei);
+    if (M > 0.0 && isfinite(M)) {
+      const int big = ilogb(M) + (Ei - En);
+      if (big > 400) En += big - 300;
+    }
+    sh_acc = E - En;
+    sh_x = Ei - En;
+    E = En;
+    return Ei;
+  };
+  const int tiles = BI / 32;
+  const bool nearcta = chain && cta >= LA_ND - tiles;
+  // B(block i-1, block i) rows of this CTA's tile of the next diagonal block
+  // (B is fixed during the solve) into Bt (32 x BI, column-major), loaded
+  // while the step's x_i is being formed
+  auto prefetch_near = [&](int i) {
+    const int tr = cta - (LA_ND - tiles);
+    const int rn = (i - 1) * BI + tr * 32, c0 = i * BI, cols = min(BI, m - c0);
+    for (int e = tid; e < 32 * cols; e += blockDim.x) {
+      const int r = e & 31, c = e >> 5;
+      cp_async8(Bt + e, Bl + (size_t)(rn + r) + (size_t)(c0 + c) * ldb);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  if (chain) {
+    int sa = 0, sx = 0;  // frame shifts of the previous step
+    for (int s = 0; s < nbk; ++s) {
+      const int i = nbk - 1 - s, r0 = i * BI, rows = min(BI, m - r0);
+      if (nearcta && i > 0) prefetch_near(i);
+      const bool sf = !force_subst && __ldcg(a.safe + i);
+      // this warp's row of the block inverse (B and its inverses are fixed
+      // during the panel), loaded before the waits: x_i(rr) = sum_q X(rr, q) acc(q)
+      const int per = (rows + LA_ND - 1) / LA_ND;  // <= BI / 32 rows per CTA, one per warp
+      const int rr = cta * per + (tid >> 5), lane = tid & 31;
+      const bool myrow = sf && (tid >> 5) < per && rr < rows;
+      double xr[BI / 32];
+      {
+        const double* Xr = a.Xinv + (size_t)i * BI * BI + (size_t)rr * rows;
+#pragma unroll
+        for (int u = 0; u < BI / 32; ++u) {
+          const int q = rr + lane + 32 * u;
+          xr[u] = (myrow && q < rows) ? __ldcg(Xr + q) : 0.0;
+        }
+      }
+      // the chain's step s-1 and the far CTAs owning the tiles of block i
+      // (tile t belongs to CTA LA_ND + t mod NF), which finished step s-2
+      if (s > 0)
+        la_wait2(a.prog, LA_ND, base + 2 * s, min(NF, BI / 32),
+                 [&](int u) { return LA_ND + (i * (BI / 32) + u) % NF; }, s > 1 ? base + s - 1 : 0ull, a.err);
+      // accumulator of block i in the frame of this step
+      for (int q = tid; q < rows; q += blockDim.x) {
+        const double av = __ldcg(accv + r0 + q);
+        xs[q] = (s == 0) ? av : ldexp(av, sa) - ldexp(__ldcg(a.nearv + q), sx);
+      }
+      __syncthreads();
+      // ---- P1: x_i ----
+      if (sf) {
+        double mx = 0.0;
+        if (myrow) {
+          double t = 0.0;
+#pragma unroll
+          for (int u = 0; u < BI / 32; ++u) {
+            const int q = rr + lane + 32 * u;
+            if (q < rows) t += xr[u] * xs[q];
+          }
+          t = ht_warp_sum(t);
+          if (lane == 0) sol[r0 + rr] = t;
+          mx = fabs(t);
+        }
+        mx = ht_block_max(mx, red);
+        if (tid == 0) { a.xmax[(size_t)i * 32 + cta] = mx; if (cta == 0) a.flags[i] = 0; }
+      } else if (cta == 0) {
+        int shift = 0;
+        subst_block(Bl, ldb, a.invd, r0, rows, xs, tile, red4, xl, shi, &shift);
+        double mx = 0.0;
+        for (int r = tid; r < rows; r += blockDim.x) { sol[r0 + r] = xs[r]; mx = fmax(mx, fabs(xs[r])); }
+        mx = ht_block_max(mx, red);
+        if (tid == 0) { a.xmax[(size_t)i * 32] = mx; a.flags[i] = shift; }
+      }
+      la_publish(a.prog + cta, base + 2 * s + 1);
+      la_wait(a.prog, LA_ND, ident, base + 2 * s + 1, a.err);
+      const int Ei = frame(i, sa, sx);
+      if (cta == 0 && tid == 0) a.exps[i] = Ei;
+      // ---- P2: nearv = B(block i-1, block i) x_i, one 32-row tile per CTA ----
+      if (i > 0 && nearcta) {
+        const int tr = cta - (LA_ND - tiles);
+        for (int q = tid; q < rows; q += blockDim.x) xs[q] = __ldcg(sol + r0 + q);
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        const int lane = tid & 31, wi = tid >> 5, nw = blockDim.x >> 5;
+        double s0 = 0.0, s1 = 0.0;
+        int c = wi;
+        for (; c + nw < rows; c += 2 * nw) {
+          s0 += Bt[c * 32 + lane] * xs[c];
+          s1 += Bt[(c + nw) * 32 + lane] * xs[c + nw];
+        }
+        if (c < rows) s0 += Bt[c * 32 + lane] * xs[c];
+        red4[tid] = s0 + s1;
+        __syncthreads();
+        if (tid < 32) {
+          double t = 0.0;
+          for (int w2 = 0; w2 < nw; ++w2) t += red4[w2 * 32 + tid];
+          a.nearv[tr * 32 + tid] = t;
+        }
+      }
+      la_publish(a.prog + cta, base + 2 * s + 2);
+    }
+  } else {
+    const int f = cta - LA_ND;
+    for (int s = 0; s + 2 < nbk; ++s) {
+      const int i = nbk - 1 - s, r0 = i * BI, rows = min(BI, m - r0);
+      const int lim = (i - 1) * BI;  // rows above the next diagonal block
+      la_wait(a.prog, LA_ND, ident, base + 2 * s + 1, a.err);
+      int sh_acc, sh_x;
+      frame(i, sh_acc, sh_x);
+      if (f * 32 < lim) {
+        for (int q = tid; q < BI; q += blockDim.x) xs[q] = (q < rows) ? __ldcg(sol + r0 + q) : 0.0;
+        __syncthreads();
+        for (int tb = f * 32; tb < lim; tb += NF * 32) {
+          const double sum = gemv32<false>(Bl, ldb, tb, 32, r0, rows, xs, red4);
+          if (tid < 32) {
+            const double av = __ldcg(accv + tb + tid);
+            accv[tb + tid] = ldexp(av, sh_acc) - ldexp(sum, sh_x);
+          }
+        }
+      }
+      la_publish(a.prog + cta, base + s + 1);
+    }
+  }
+}
+
 template <bool STAGE>
 __global__ void __launch_bounds__(HT_THREADS, 1) panel_kernel(PanelArgs a) {
   cg::grid_group grid = cg::this_grid();
@@ -594,7 +858,16 @@ __global__ void __launch_bounds__(HT_THREADS, 1) panel_kernel(PanelArgs a) {
       grid.sync();
       PHASE_MARK(3);
       // ---- Phase E: scaled backward substitution B y~ = 2^-E c~ ----
-      trsv_gs(a, grid, m, a.ctil, a.ytil, a.w, subst_mode, tile, red4, acc, xl, xs, red, shi);
+      if (G >= 2 * LA_ND) {
+        {
+          const int ch = (m + G - 1) / G, rb = min(m, cta * ch), re = min(m, rb + ch);
+          for (int r = rb + tid; r < re; r += blockDim.x) a.w[r] = __ldcg(a.ctil + r);
+        }
+        grid.sync();
+        trsv_la(a, m, a.w, a.ytil, subst_mode, epoch, tile, red4, xl, xs, red, shi, Dsm);
+      } else {
+        trsv_gs(a, grid, m, a.ctil, a.ytil, a.w, subst_mode, tile, red4, acc, xl, xs, red, shi);
+      }
       ++epoch;
       grid.sync();
     PHASE_MARK(4);
@@ -686,22 +959,29 @@ __global__ void __launch_bounds__(HT_THREADS, 1) panel_kernel(PanelArgs a) {
       grid.sync();
     PHASE_MARK(8);
       // ---- Phase J: w2 = B w as chunk partials over the upper staircase ----
-      // items (column chunk ch of CWC columns, row tile rb of BS rows) with
-      // rb * BS < (ch + 1) * CWC, assigned round-robin to CTAs
+      // items (column chunk ch of CWC columns, row tile rb of 32 rows) with
+      // rb * 32 < (ch + 1) * CWC, assigned round-robin to CTAs; wide chunks
+      // keep each CTA streaming for long stretches (the diagonal chunks also
+      // multiply the zeros below the diagonal: m CWC / 2 extra entries)
       {
-        constexpr int CWC = 4 * BS;
+        constexpr int CWC = HT_TRMV_CW;
         constexpr int RPC = CWC / 32;  // 32-row tiles per column chunk on the diagonal
         const double* Bl = a.B + (size_t)(s + 1) + (size_t)(s + 1) * a.ldb;
         const int nrb = (m + 31) / 32, nchk = (m + CWC - 1) / CWC;
         int total = 0;
         for (int ch = 0; ch < nchk; ++ch) total += min(nrb, RPC * (ch + 1));
-        int ch = 0, base = 0;
+        int ch = 0, base = 0, staged = -1;
         for (int item = cta; item < total; item += G) {
           while (item >= base + min(nrb, RPC * (ch + 1))) { base += min(nrb, RPC * (ch + 1)); ++ch; }
           const int rb = item - base;
           const int r0 = rb * 32, rows = min(32, m - r0);
           const int cc = ch * CWC, cols = min(CWC, m - cc);
-          const double sum = gemv32<true>(Bl, a.ldb, r0, rows, cc, cols, a.w + cc, red4);
+          if (ch != staged) {  // w(chunk) into shared memory (the inversion scratch is free here)
+            for (int c = tid; c < cols; c += blockDim.x) Dsm[c] = __ldcg(a.w + cc + c);
+            __syncthreads();
+            staged = ch;
+          }
+          const double sum = gemv32<false>(Bl, a.ldb, r0, rows, cc, cols, Dsm, red4);
           if (tid < rows) a.wpart[(size_t)ch * n + r0 + tid] = sum;
         }
       }
@@ -709,7 +989,7 @@ __global__ void __launch_bounds__(HT_THREADS, 1) panel_kernel(PanelArgs a) {
       PHASE_MARK(9);
       // ---- Phase K1: w2 rows of this CTA, partial U^T w2 ----
       {
-        constexpr int CWC = 4 * BS;
+        constexpr int CWC = HT_TRMV_CW;
         const int nchk = (m + CWC - 1) / CWC;
         for (int r = rbeg + tid; r < rend; r += blockDim.x) {
           double v = 0.0;
@@ -812,11 +1092,22 @@ __global__ void __launch_bounds__(HT_THREADS, 1) panel_kernel(PanelArgs a) {
       const int cw = (p + nch - 1) / nch;
       const double* Ab = a.A + (size_t)(s + 1) + (size_t)(j + 1) * a.lda;
       const double* vk = a.z + k;  // v(k + c) for column j+1+c
+      int staged = -1;
       for (int item = cta; item < nrb * nch; item += G) {
         const int rb = item % nrb, ch = item / nrb;
         const int r0 = rb * 32, rows = min(32, m - r0);
         const int c0 = ch * cw, cols = max(0, min(cw, p - c0));
-        const double sum = gemv32<true>(Ab, a.lda, r0, rows, c0, cols, vk + c0, red4);
+        double sum;
+        if (cw <= 32 * BI) {  // v(chunk) into shared memory (the inversion scratch is free here)
+          if (ch != staged) {
+            for (int c = tid; c < cols; c += blockDim.x) Dsm[c] = __ldcg(vk + c0 + c);
+            __syncthreads();
+            staged = ch;
+          }
+          sum = gemv32<false>(Ab, a.lda, r0, rows, c0, cols, Dsm, red4);
+        } else {
+          sum = gemv32<true>(Ab, a.lda, r0, rows, c0, cols, vk + c0, red4);
+        }
         if (tid < rows) a.ypart[(size_t)ch * n + r0 + tid] = sum;
       }
       // chunks never visited for a row stay unused: the reduction below reads nch chunks
@@ -971,11 +1262,11 @@ cudaError_t ht_launch_panel(HtWork& w, double* A, int lda, const double* B, int 
   a.epoch0 = w.epoch_host;
   a.st = w.status; a.err = w.err; a.bnorm = w.bnorm;
   // epochs used: at most kmax * (max_ir + 1) solves
-  w.epoch_host += (unsigned)(kmax * (max_ir + 1) + 1);
+  w.epoch_host += (unsigned)((kmax + 1) * (max_ir + 1) + 1);
   const int m = w.n - s - 1;
   a.cap = (m + w.G - 1) / w.G;
   a.ptime = w.ptime;
-  a.Xinv = w.Xinv; a.safe = w.safe; a.xmax = w.xmax; a.wpart = w.wpart;
+  a.Xinv = w.Xinv; a.safe = w.safe; a.xmax = w.xmax; a.prog = w.prog; a.nearv = w.nearv; a.wpart = w.wpart;
   size_t smem = smem_doubles(w.nb, a.cap) * sizeof(double);
   a.stage = smem <= (size_t)kPanelSmemMax - 4096;
   if (!a.stage) smem = smem_base_doubles(w.nb) * sizeof(double);
