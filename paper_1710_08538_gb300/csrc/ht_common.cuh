@@ -136,6 +136,8 @@ struct HtWork {
   double* rtaus;           // tau of every restore step (n + 2 HT_NB_MAX)
   void* emu_dig;           // digits of Vw / Ww for the emulated sweeps (emu_cap windows)
   int* emu_exps;           // their exponent bounds (2 per window)
+  double* emu_mwy;         // merged windows of small-k chains (ht_emu_merge_doubles(emu_cap))
+  void* emu_geo;           // their table (emu_cap int4)
   int emu_cap;             // windows per launch of the emulated sweeps
   int prec;                // HT_PREC_* of the current call
   cudaStream_t stream;
@@ -177,10 +179,13 @@ struct HtSweepJob {
 cudaError_t ht_sweep_multi(cudaStream_t st, const HtSweepJob* jobs, int njobs, const double* wy, long stride, int mode,
                            int p, int k, int t0, int t1);
 // as ht_sweep_multi with FP64 emulated on the tensor cores (ht_emu.cu); needs
-// k <= 32 and a digit buffer of `cap` windows of ht_emu_window_bytes(k) each
+// k <= 32, a digit buffer of `cap` windows of ht_emu_window_bytes(k) each and,
+// to merge the windows of chains with k <= 16, ht_emu_merge_doubles(cap)
+// doubles at mwy and cap int4 at geo (null: no merging)
 cudaError_t ht_emu_sweep_multi(cudaStream_t st, const HtSweepJob* jobs, int njobs, const double* wy, long stride, int mode,
-                               int p, int k, int t0, int t1, void* dig, int* exps, int cap);
+                               int p, int k, int t0, int t1, void* dig, int* exps, int cap, double* mwy, void* geo);
 size_t ht_emu_window_bytes(int nb);
+size_t ht_emu_merge_doubles(int cap);
 cudaError_t ht_sweep(cudaStream_t st, int right, double* X, long ldx, int line0, int nlines, int origin,
                      const double* wy, long stride, int mode, int p, int k, int t0, int t1, int use_limit,
                      int limit_base);

@@ -51,10 +51,16 @@ constexpr int ETH = 256;   // threads per CTA (8 warps)
 // ---------------------------------------------------------------------------
 // Window geometry (the same as the FP64 sweeps; see ht_apply.cu)
 // ---------------------------------------------------------------------------
+// mode EMU_MERGED: windows of a merged chain, geometry from the table geo
+// (offset, width, reflectors, limit) written by emu_merge_kernel.
+constexpr int EMU_MERGED = 4;
 __device__ __forceinline__ void emu_win_geom(int mode, int p, int k, int t, int* off, int* width, int* nrefl,
-                                             int* limit) {
+                                             int* limit, const int4* geo = nullptr) {
   int a, b;
-  if (mode == 0) {
+  if (mode == EMU_MERGED) {
+    const int4 g = geo[t];
+    *off = g.x; *width = g.y; *nrefl = g.z; *limit = g.w;
+  } else if (mode == 0) {
     ht_ql_window(p, k, t, &a, &b);
     *off = a; *width = b - a; *nrefl = k; *limit = b;
   } else if (mode == 1) {
@@ -203,12 +209,12 @@ struct EmuDims {
 
 template <int KPAD>
 __global__ void __launch_bounds__(ETH) emu_prep_kernel(const double* wy, long stride, int mode, int p, int k, int t0,
-                                                       uint2* dig, int* exps) {
+                                                       uint2* dig, int* exps, const int4* geo) {
   using D = EmuDims<KPAD>;
   __shared__ int fmax[2];
   const int t = t0 + blockIdx.x;
   int off, w, kr, lim;
-  emu_win_geom(mode, p, k, t, &off, &w, &kr, &lim);
+  emu_win_geom(mode, p, k, t, &off, &w, &kr, &lim, geo);
   const double* Vw = wy + (size_t)t * stride;
   const double* Ww = Vw + stride / 2;
   if (threadIdx.x < 2) fmax[threadIdx.x] = 1;
@@ -276,6 +282,7 @@ struct EmuBatch {
   int mode, p, k, t0, t1;
   const uint2* dig;  // digits of windows t0 .. t1-1
   const int* exps;
+  const int4* geo;   // window table (mode EMU_MERGED)
 };
 
 template <int KPAD>
@@ -326,7 +333,7 @@ __global__ void __launch_bounds__(ETH) emu_sweep_kernel(EmuBatch b) {
 
   for (int t = b.t0; t < b.t1; ++t) {
     int off, w, kr, lim;
-    emu_win_geom(b.mode, b.p, b.k, t, &off, &w, &kr, &lim);
+    emu_win_geom(b.mode, b.p, b.k, t, &off, &w, &kr, &lim, b.geo);
     if (jb.right) {
       if (jb.use_limit && lb >= jb.limit_base + lim) continue;
     } else {
@@ -473,6 +480,81 @@ __global__ void __launch_bounds__(ETH) emu_sweep_kernel(EmuBatch b) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Merged windows for chains with few reflectors per window (k <= 16).  The
+// chain's transforms are applied in order, x <- x G_t G_{t+1} ..., and the
+// product of g consecutive ones is again of the form I - V' W'^T on the union
+// of their rows: for two, (I - V1 W1^T)(I - V2 W2^T) = I - [V1, V2 - V1 C]
+// [W1, W2]^T with C = W1^T V2.  Merging g = floor(32 / k) windows gives
+// blocks of at most (g + 1) k <= 48 rows and g k <= 32 columns, which the
+// KPAD = 32 kernels apply as one dense window instead of g thin ones.  The
+// chain itself (its windows and their order) is the one of Sec. 3.3.
+// One CTA per merged window, FP64 in shared memory; output: V' at
+// mwy + m * EMU_MSTRIDE (ld = width), W' at + EMU_MSTRIDE / 2, and the table
+// geo[m] = (offset, width, columns, limit), the limit being the largest (mode 0)
+// or smallest (mode 1) of the merged windows' so that no line the windows
+// update is skipped.
+// ---------------------------------------------------------------------------
+constexpr int EMU_MROWS = 64, EMU_MCOLS = 32;
+constexpr long EMU_MSTRIDE = 2L * EMU_MROWS * EMU_MCOLS;
+
+__global__ void __launch_bounds__(ETH) emu_merge_kernel(const double* wy, long stride, int mode, int p, int k, int g,
+                                                        int ta0, int t1, double* mwy, int4* geo) {
+  __shared__ double Va[EMU_MROWS * EMU_MCOLS], Wa[EMU_MROWS * EMU_MCOLS], Cm[EMU_MCOLS * EMU_MCOLS];
+  __shared__ int gq[4];
+  const int tid = threadIdx.x;
+  const int ta = ta0 + blockIdx.x * g, tb = min(t1, ta + g);
+  if (tid == 0) {
+    int o0 = 1 << 30, e0 = -1, kt = 0, lm = 0;
+    for (int t = ta; t < tb; ++t) {
+      int off, w, kr, lim;
+      emu_win_geom(mode, p, k, t, &off, &w, &kr, &lim);
+      o0 = min(o0, off);
+      e0 = max(e0, off + w);
+      kt += kr;
+      lm = (t == ta) ? lim : (mode == 1 ? min(lm, lim) : max(lm, lim));
+    }
+    gq[0] = o0; gq[1] = e0 - o0; gq[2] = kt; gq[3] = lm;
+  }
+  for (int e = tid; e < EMU_MROWS * EMU_MCOLS; e += blockDim.x) { Va[e] = 0.0; Wa[e] = 0.0; }
+  __syncthreads();
+  const int o0 = gq[0], wp = gq[1], kp = gq[2];
+  int r = 0;  // columns merged so far
+  for (int t = ta; t < tb; ++t) {
+    int off, w, kr, lim;
+    emu_win_geom(mode, p, k, t, &off, &w, &kr, &lim);
+    const double* Vw = wy + (size_t)t * stride;
+    const double* Ww = Vw + stride / 2;
+    const int ro = off - o0;
+    // C = Wa(:, 0:r)^T V_t (r x kr); V_t lives on rows [ro, ro + w) of the union
+    for (int e = tid; e < r * kr; e += blockDim.x) {
+      const int i = e % r, c = e / r;
+      double acc = 0.0;
+      for (int q = 0; q < w; ++q) acc += Wa[(ro + q) + i * EMU_MROWS] * Vw[q + (size_t)c * w];
+      Cm[i + c * EMU_MCOLS] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < wp * kr; e += blockDim.x) {
+      const int row = e % wp, c = e / wp;
+      const bool in = row >= ro && row < ro + w;
+      double v = in ? Vw[(row - ro) + (size_t)c * w] : 0.0;
+      for (int i = 0; i < r; ++i) v -= Va[row + i * EMU_MROWS] * Cm[i + c * EMU_MCOLS];
+      Va[row + (r + c) * EMU_MROWS] = v;
+      Wa[row + (r + c) * EMU_MROWS] = in ? Ww[(row - ro) + (size_t)c * w] : 0.0;
+    }
+    __syncthreads();
+    r += kr;
+  }
+  double* Vo = mwy + (size_t)blockIdx.x * EMU_MSTRIDE;
+  double* Wo = Vo + EMU_MSTRIDE / 2;
+  for (int e = tid; e < wp * kp; e += blockDim.x) {
+    const int row = e % wp, c = e / wp;
+    Vo[e] = Va[row + c * EMU_MROWS];
+    Wo[e] = Wa[row + c * EMU_MROWS];
+  }
+  if (tid == 0) geo[blockIdx.x] = make_int4(gq[0], gq[1], gq[2], gq[3]);
+}
+
 template <int KPAD>
 cudaError_t emu_attr() {
   static std::mutex mu;
@@ -490,7 +572,7 @@ cudaError_t emu_attr() {
 
 template <int KPAD>
 cudaError_t emu_run(cudaStream_t st, const HtSweepJob* jobs, int njobs, const double* wy, long stride, int mode, int p,
-                    int k, int t0, int t1, uint2* dig, int* exps, int cap) {
+                    int k, int t0, int t1, uint2* dig, int* exps, int cap, const int4* geo = nullptr) {
   using D = EmuDims<KPAD>;
   cudaError_t e = emu_attr<KPAD>();
   if (e != cudaSuccess) return e;
@@ -505,10 +587,10 @@ cudaError_t emu_run(cudaStream_t st, const HtSweepJob* jobs, int njobs, const do
     ctas += (jobs[i].nlines + ER - 1) / ER;
   }
   if (nj == 0) return cudaSuccess;
-  b.njobs = nj; b.mode = mode; b.p = p; b.k = k; b.dig = dig; b.exps = exps;
+  b.njobs = nj; b.mode = mode; b.p = p; b.k = k; b.dig = dig; b.exps = exps; b.geo = geo;
   for (int c0 = t0; c0 < t1; c0 += cap) {
     const int c1 = std::min(t1, c0 + cap);
-    emu_prep_kernel<KPAD><<<c1 - c0, ETH, 0, st>>>(wy, stride, mode, p, k, c0, dig, exps);
+    emu_prep_kernel<KPAD><<<c1 - c0, ETH, 0, st>>>(wy, stride, mode, p, k, c0, dig, exps, geo);
     b.t0 = c0; b.t1 = c1;
     emu_sweep_kernel<KPAD><<<ctas, ETH, EmuSmem<KPAD>::BYTES, st>>>(b);
     e = cudaGetLastError();
@@ -520,13 +602,31 @@ cudaError_t emu_run(cudaStream_t st, const HtSweepJob* jobs, int njobs, const do
 }  // namespace
 
 size_t ht_emu_window_bytes(int nb) {
-  return (nb <= 16 ? (size_t)EmuDims<16>::WIN : (size_t)EmuDims<32>::WIN) * sizeof(uint2);
+  (void)nb;  // merged windows of small-k chains use the KPAD = 32 layout
+  return (size_t)EmuDims<32>::WIN * sizeof(uint2);
 }
+size_t ht_emu_merge_doubles(int cap) { return (size_t)cap * EMU_MSTRIDE; }
 
 cudaError_t ht_emu_sweep_multi(cudaStream_t st, const HtSweepJob* jobs, int njobs, const double* wy, long stride, int mode,
-                               int p, int k, int t0, int t1, void* dig, int* exps, int cap) {
+                               int p, int k, int t0, int t1, void* dig, int* exps, int cap, double* mwy, void* geo) {
   if (njobs < 1 || njobs > HT_SWEEP_MAXJOBS) return cudaErrorInvalidValue;
   if (t1 <= t0) return cudaSuccess;
+  const int g = k >= 1 ? 32 / k : 1;
+  if (g >= 2 && mwy && geo) {
+    // merged windows, at most cap of them per round (the buffers hold cap)
+    const int nm = (t1 - t0 + g - 1) / g;
+    for (int m0 = 0; m0 < nm; m0 += cap) {
+      const int mc = std::min(cap, nm - m0);
+      const int ta = t0 + m0 * g, tb = std::min(t1, ta + mc * g);
+      emu_merge_kernel<<<mc, ETH, 0, st>>>(wy, stride, mode, p, k, g, ta, tb, mwy, (int4*)geo);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      e = emu_run<32>(st, jobs, njobs, mwy, EMU_MSTRIDE, EMU_MERGED, p, k, 0, mc, (uint2*)dig, exps, cap,
+                      (const int4*)geo);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   if (k <= 16) return emu_run<16>(st, jobs, njobs, wy, stride, mode, p, k, t0, t1, (uint2*)dig, exps, cap);
   if (k <= 32) return emu_run<32>(st, jobs, njobs, wy, stride, mode, p, k, t0, t1, (uint2*)dig, exps, cap);
   return cudaErrorNotSupported;
