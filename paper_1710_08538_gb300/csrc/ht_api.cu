@@ -89,8 +89,9 @@ size_t ht_layout_work(HtWork& w, char* b, int n, int nb, int G, unsigned long lo
   w.emu_cap = std::min(n / 32 + 4, 1024);
   const size_t oEmu = take(emu_win ? (emu_win * w.emu_cap + sizeof(double) - 1) / sizeof(double) : 0);
   const size_t oEmuE = take((size_t)w.emu_cap);
-  const size_t oEmuM = take(emu_win ? ht_emu_merge_doubles(w.emu_cap) : 0);
-  const size_t oEmuG = take(emu_win ? 2 * (size_t)w.emu_cap : 0);  // int4 = 2 doubles
+  // merged windows of chains with k <= 16 (both precisions)
+  const size_t oEmuM = take(ht_emu_merge_doubles(w.emu_cap));
+  const size_t oEmuG = take(2 * (size_t)w.emu_cap);  // int4 = 2 doubles
   const size_t oRc = take(2);
   const size_t oRt = take(nn + 2 * HT_NB_MAX);
   if (!b) return total;
@@ -124,8 +125,8 @@ size_t ht_layout_work(HtWork& w, char* b, int n, int nb, int G, unsigned long lo
   w.nearv = (double*)(b + oNear);
   w.emu_dig = emu_win ? (void*)(b + oEmu) : nullptr;
   w.emu_exps = (int*)(b + oEmuE);
-  w.emu_mwy = emu_win ? (double*)(b + oEmuM) : nullptr;
-  w.emu_geo = emu_win ? (void*)(b + oEmuG) : nullptr;
+  w.emu_mwy = (double*)(b + oEmuM);
+  w.emu_geo = (void*)(b + oEmuG);
   w.rcount = (int*)(b + oRc);
   w.rtaus = (double*)(b + oRt);
   w.wpart = (double*)(b + oWpart);
@@ -297,7 +298,7 @@ cudaError_t run_sweep(Ctx& c, const HtSweepJob* jobs, int njobs, const double* w
   if (c.w->prec == HT_PREC_EMU)
     return ht_emu_sweep_multi(c.st, jobs, njobs, wy, wst, mode, p, k, t0, t1, c.w->emu_dig, c.w->emu_exps,
                               c.w->emu_cap, c.w->emu_mwy, c.w->emu_geo);
-  return ht_sweep_multi(c.st, jobs, njobs, wy, wst, mode, p, k, t0, t1);
+  return ht_sweep_multi(c.st, jobs, njobs, wy, wst, mode, p, k, t0, t1, c.w->emu_mwy, c.w->emu_geo, c.w->emu_cap);
 }
 
 // Absorption of k right and k left reflectors (Sec. 3.3.1 and 3.3.2).

@@ -176,8 +176,15 @@ struct HtSweepJob {
   int use_limit;   // 1: skip stripes that the structural limit says are zero
   int limit_base;  // added to the window limit
 };
+// mwy, geo, cap: buffers of ht_merge_windows (null: no merging) for chains with k <= 16
 cudaError_t ht_sweep_multi(cudaStream_t st, const HtSweepJob* jobs, int njobs, const double* wy, long stride, int mode,
-                           int p, int k, int t0, int t1);
+                           int p, int k, int t0, int t1, double* mwy, void* geo, int cap);
+// products of g consecutive window transforms of windows [ta, tb) of a chain
+// (mode 0-3), one merged window per g: V', W' at mwy + m * ht_merge_stride()
+// (W' at + ht_merge_stride() / 2) and the int4 table geo[m] (ht_emu.cu)
+cudaError_t ht_merge_windows(cudaStream_t st, const double* wy, long stride, int mode, int p, int k, int g, int ta,
+                             int tb, double* mwy, void* geo);
+long ht_merge_stride();
 // as ht_sweep_multi with FP64 emulated on the tensor cores (ht_emu.cu); needs
 // k <= 32, a digit buffer of `cap` windows of ht_emu_window_bytes(k) each and,
 // to merge the windows of chains with k <= 16, ht_emu_merge_doubles(cap)

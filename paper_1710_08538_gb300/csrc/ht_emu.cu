@@ -606,6 +606,14 @@ size_t ht_emu_window_bytes(int nb) {
   return (size_t)EmuDims<32>::WIN * sizeof(uint2);
 }
 size_t ht_emu_merge_doubles(int cap) { return (size_t)cap * EMU_MSTRIDE; }
+long ht_merge_stride() { return EMU_MSTRIDE; }
+cudaError_t ht_merge_windows(cudaStream_t st, const double* wy, long stride, int mode, int p, int k, int g, int ta,
+                             int tb, double* mwy, void* geo) {
+  if (tb <= ta) return cudaSuccess;
+  const int nm = (tb - ta + g - 1) / g;
+  emu_merge_kernel<<<nm, ETH, 0, st>>>(wy, stride, mode, p, k, g, ta, tb, mwy, (int4*)geo);
+  return cudaGetLastError();
+}
 
 cudaError_t ht_emu_sweep_multi(cudaStream_t st, const HtSweepJob* jobs, int njobs, const double* wy, long stride, int mode,
                                int p, int k, int t0, int t1, void* dig, int* exps, int cap, double* mwy, void* geo) {
@@ -618,8 +626,7 @@ cudaError_t ht_emu_sweep_multi(cudaStream_t st, const HtSweepJob* jobs, int njob
     for (int m0 = 0; m0 < nm; m0 += cap) {
       const int mc = std::min(cap, nm - m0);
       const int ta = t0 + m0 * g, tb = std::min(t1, ta + mc * g);
-      emu_merge_kernel<<<mc, ETH, 0, st>>>(wy, stride, mode, p, k, g, ta, tb, mwy, (int4*)geo);
-      cudaError_t e = cudaGetLastError();
+      cudaError_t e = ht_merge_windows(st, wy, stride, mode, p, k, g, ta, tb, mwy, geo);
       if (e != cudaSuccess) return e;
       e = emu_run<32>(st, jobs, njobs, mwy, EMU_MSTRIDE, EMU_MERGED, p, k, 0, mc, (uint2*)dig, exps, cap,
                       (const int4*)geo);
