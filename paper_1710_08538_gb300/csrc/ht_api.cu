@@ -89,7 +89,7 @@ size_t ht_layout_work(HtWork& w, char* b, int n, int nb, int G, unsigned long lo
   w.emu_cap = std::min(n / 32 + 4, 1024);
   const size_t oEmu = take(emu_win ? (emu_win * w.emu_cap + sizeof(double) - 1) / sizeof(double) : 0);
   const size_t oEmuE = take((size_t)w.emu_cap);
-  // merged windows of chains with k <= 16 (both precisions)
+  // merged windows of the emulated sweeps of chains with k <= 16
   const size_t oEmuM = take(ht_emu_merge_doubles(w.emu_cap));
   const size_t oEmuG = take(2 * (size_t)w.emu_cap);  // int4 = 2 doubles
   const size_t oRc = take(2);
@@ -298,7 +298,9 @@ cudaError_t run_sweep(Ctx& c, const HtSweepJob* jobs, int njobs, const double* w
   if (c.w->prec == HT_PREC_EMU)
     return ht_emu_sweep_multi(c.st, jobs, njobs, wy, wst, mode, p, k, t0, t1, c.w->emu_dig, c.w->emu_exps,
                               c.w->emu_cap, c.w->emu_mwy, c.w->emu_geo);
-  return ht_sweep_multi(c.st, jobs, njobs, wy, wst, mode, p, k, t0, t1, c.w->emu_mwy, c.w->emu_geo, c.w->emu_cap);
+  // the FP64 sweeps take the windows one by one: they are DFMA-bound, and a merged window
+  // of g windows multiplies their flops by about g / 2
+  return ht_sweep_multi(c.st, jobs, njobs, wy, wst, mode, p, k, t0, t1);
 }
 
 // Absorption of k right and k left reflectors (Sec. 3.3.1 and 3.3.2).

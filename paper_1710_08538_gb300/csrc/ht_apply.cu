@@ -79,7 +79,6 @@ struct SweepBatch {
   long stride;     // doubles between consecutive windows of the WY store (Ww at stride / 2)
   int mode, p, k, t0, t1;
   int ex_off, ex_width, ex_nrefl;  // mode 4
-  const int4* geo;                 // mode 5: window table (merged windows)
 };
 
 // Right application to rows [line0 + stripe*SR, ...) of X, X(:, c) <- X(:, c) G.
@@ -97,7 +96,6 @@ __device__ void sweep_right_body(const SweepBatch& b, const SweepJob& jb, int st
   for (int t = b.t0; t < b.t1; ++t) {
     int off, w, kr, lim;
     if (b.mode == 4) { off = b.ex_off; w = b.ex_width; kr = b.ex_nrefl; lim = 0; }
-    else if (b.mode == 5) { const int4 g = b.geo[t]; off = g.x; w = g.y; kr = g.z; lim = g.w; }
     else win_geom(b.mode, b.p, b.k, t, &off, &w, &kr, &lim);
     if (jb.use_limit && row_begin >= jb.limit_base + lim) continue;
     const double* Vw = b.wy + (size_t)t * b.stride;
@@ -154,7 +152,6 @@ __device__ void sweep_left_body(const SweepBatch& b, const SweepJob& jb, int str
   for (int t = b.t0; t < b.t1; ++t) {
     int off, w, kr, lim;
     if (b.mode == 4) { off = b.ex_off; w = b.ex_width; kr = b.ex_nrefl; lim = 0; }
-    else if (b.mode == 5) { const int4 g = b.geo[t]; off = g.x; w = g.y; kr = g.z; lim = g.w; }
     else win_geom(b.mode, b.p, b.k, t, &off, &w, &kr, &lim);
     if (jb.use_limit && col_end <= jb.limit_base + lim) continue;
     const double* Vw = b.wy + (size_t)t * b.stride;
@@ -483,25 +480,7 @@ static cudaError_t launch_batch(cudaStream_t st, SweepBatch& b, const HtSweepJob
 }
 
 cudaError_t ht_sweep_multi(cudaStream_t st, const HtSweepJob* jobs, int njobs, const double* wy, long stride, int mode,
-                           int p, int k, int t0, int t1, double* mwy, void* geo, int cap) {
-  const int g = k >= 1 ? 32 / k : 1;
-  if (g >= 2 && mwy && geo && cap > 0 && t1 > t0) {
-    // chains with few reflectors per window: products of g consecutive window
-    // transforms (ht_merge_windows), at most cap per round
-    const int nm = (t1 - t0 + g - 1) / g;
-    for (int m0 = 0; m0 < nm; m0 += cap) {
-      const int mc = nm - m0 < cap ? nm - m0 : cap;
-      const int ta = t0 + m0 * g, tb = t1 < ta + mc * g ? t1 : ta + mc * g;
-      cudaError_t e = ht_merge_windows(st, wy, stride, mode, p, k, g, ta, tb, mwy, geo);
-      if (e != cudaSuccess) return e;
-      SweepBatch b{};
-      b.wy = mwy; b.stride = ht_merge_stride(); b.mode = 5; b.p = p; b.k = k; b.t0 = 0; b.t1 = mc;
-      b.geo = (const int4*)geo;
-      e = launch_batch(st, b, jobs, njobs);
-      if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-  }
+                           int p, int k, int t0, int t1) {
   SweepBatch b{};
   b.wy = wy; b.stride = stride; b.mode = mode; b.p = p; b.k = k; b.t0 = t0; b.t1 = t1;
   return launch_batch(st, b, jobs, njobs);
@@ -511,7 +490,7 @@ cudaError_t ht_sweep(cudaStream_t st, int right, double* X, long ldx, int line0,
                      const double* wy, long stride, int mode, int p, int k, int t0, int t1, int use_limit,
                      int limit_base) {
   const HtSweepJob j{X, ldx, right, line0, nlines, origin, use_limit, limit_base};
-  return ht_sweep_multi(st, &j, 1, wy, stride, mode, p, k, t0, t1, nullptr, nullptr, 0);
+  return ht_sweep_multi(st, &j, 1, wy, stride, mode, p, k, t0, t1);
 }
 
 cudaError_t ht_apply_single(cudaStream_t st, int right, double* X, long ldx, int line0, int nlines, int origin,

@@ -176,9 +176,8 @@ struct HtSweepJob {
   int use_limit;   // 1: skip stripes that the structural limit says are zero
   int limit_base;  // added to the window limit
 };
-// mwy, geo, cap: buffers of ht_merge_windows (null: no merging) for chains with k <= 16
 cudaError_t ht_sweep_multi(cudaStream_t st, const HtSweepJob* jobs, int njobs, const double* wy, long stride, int mode,
-                           int p, int k, int t0, int t1, double* mwy, void* geo, int cap);
+                           int p, int k, int t0, int t1);
 // products of g consecutive window transforms of windows [ta, tb) of a chain
 // (mode 0-3), one merged window per g: V', W' at mwy + m * ht_merge_stride()
 // (W' at + ht_merge_stride() / 2) and the int4 table geo[m] (ht_emu.cu)
