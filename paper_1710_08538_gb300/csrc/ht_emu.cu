@@ -634,7 +634,6 @@ cudaError_t ht_emu_sweep_multi(cudaStream_t st, const HtSweepJob* jobs, int njob
     }
     return cudaSuccess;
   }
-  if (k <= 16) return emu_run<16>(st, jobs, njobs, wy, stride, mode, p, k, t0, t1, (uint2*)dig, exps, cap);
   if (k <= 32) return emu_run<32>(st, jobs, njobs, wy, stride, mode, p, k, t0, t1, (uint2*)dig, exps, cap);
   return cudaErrorNotSupported;
 }
