@@ -46,6 +46,25 @@ def f_nom(n: int) -> float:
     return 116.0 * n ** 3 / 3.0
 
 
+def max_over_ranks(ms: float, device) -> float:
+    """The slowest rank's timed interval (ms), on every rank: ranks time the
+    same number of steps concurrently, so the job took the longest of them.
+    A no-op without an initialised process group of more than one rank."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    return float(t.item())
+
+
+def job_value(world: int, steps: int, n: int, ms: float) -> float:
+    """Whole-job TFLOP/s: each of `world` ranks reduced `steps` pencils of
+    order n (replicas, weak scaling) within the slowest rank's `ms`."""
+    return world * steps * f_nom(n) / (ms / 1e3) / 1e12
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -258,14 +277,9 @@ def run_ours(args):
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.barrier()
-    ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
     sec_per_pencil = ms / 1e3 / args.steps  # per rank; ranks run concurrently
-    value = world * args.steps * f_nom(n) / (ms / 1e3) / 1e12
+    value = job_value(world, args.steps, n, ms)
 
     # backward error of the last step (probes: exact FP64 GEMMs would take minutes)
     rep = check.invariants(A0, B0, A, B, Q, Z, probes=16, seed=7)
