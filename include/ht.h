@@ -53,7 +53,7 @@ enum {
 /* Precision of the bulk (level-3) updates of the absorption, Sec. 3.3. */
 enum {
   HT_PREC_FP64 = 0, /* native FP64 (DFMA) */
-  HT_PREC_EMU = 1   /* FP64 emulated by split BF16 products on tensor cores */
+  HT_PREC_EMU = 1   /* FP64 emulated by exact FP16 digit products on the tensor cores (nb <= 32) */
 };
 
 /* Tuning and test options of ht_reduce_ex.  Zero-initialise, then set
@@ -63,7 +63,8 @@ typedef struct ht_options {
   int max_ir;          /* iterative-refinement steps per column (Sec. 2.3); default 10, < 0 means 0 */
   double ir_tol_scale; /* multiplies the IR tolerance 2u||B||_F; default 1.0, < 0 means 0 */
   int precision;       /* HT_PREC_*; default HT_PREC_FP64 */
-  int emu_slices;      /* BF16 slices per operand for HT_PREC_EMU; 0 = automatic */
+  int emu_slices;      /* HT_PREC_EMU digits of the line operand: 0 = automatic (6); 6; other values
+                          return HT_ERR_NOT_IMPLEMENTED (the WY factors always take 7) */
   uint64_t seed;       /* key of the singular-B perturbation (Remark 2.2) */
   int profile;         /* 1: time every launch by class into ht_stats (adds syncs) */
   int reserved[7];
