@@ -13,7 +13,7 @@ s the first unreduced column of A and k = j - s delayed reflectors:
 Every orthogonal factor of the absorption chains is formed as an explicit
 dense matrix (no WY blocking): this module is for checking, not speed.
 
-Readings where the paper is silent (each listed in the design doc):
+Readings where the paper is silent:
   * Householder sign: DLARFG rule (alpha = -sign(x0)||x||, identity when the
     tail is exactly zero).
   * IR tolerance 2u||B||_F with u = 2^-53 and ||B||_F of the input B; "abort
