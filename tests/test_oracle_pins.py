@@ -89,6 +89,38 @@ def test_philox_normal_is_standard_normal(oracle_lib):
     assert oracle.philox_normal(7, 3, 9) != oracle.philox_normal(8, 3, 9)
 
 
+def _philox_kat():
+    rows = []
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    for ln in open(path):
+        ln = ln.split("#")[0].split()
+        if ln:
+            w = [int(x, 16) for x in ln]
+            rows.append((w[0:4], w[4:6], w[6:10]))
+    return rows
+
+
+def test_philox4x32_10_known_answers(oracle_lib):
+    """The counter-based generator behind the Remark 2.2 perturbation is
+    Philox4x32-10: its raw blocks equal the published known-answer vectors
+    (a wrong multiplier, Weyl constant, round count or word order fails)."""
+    kat = _philox_kat()
+    assert len(kat) == 3
+    for ctr, key, out in kat:
+        assert oracle.philox4x32_10(ctr, key) == out
+
+
+def test_philox_normal_uses_first_two_words(oracle_lib):
+    """Seed 0, column 0, index 0 is the all-zero counter and key of the first
+    known-answer vector; the sample is Box-Muller on its words 0 and 1."""
+    ctr, key, out = _philox_kat()[0]
+    assert ctr == [0, 0, 0, 0] and key == [0, 0]
+    u1 = (out[0] + 1.0) * 2.0 ** -32
+    u2 = out[1] * 2.0 ** -32
+    z = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+    assert abs(oracle.philox_normal(0, 0, 0) - z) <= 1e-15 * max(1.0, abs(z))
+
+
 # --------------------------------------------------------------------------
 # Exact special cases
 # --------------------------------------------------------------------------
