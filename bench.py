@@ -78,6 +78,8 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=1024)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--budget", type=float, default=1650.0,
+                   help="wall-clock seconds the whole run must fit; fewer warm-up, then timed, steps if needed")
     return p.parse_args()
 
 
@@ -118,42 +120,58 @@ def roofline(cls: str, flops: float, ms: float, launches: int, precision: str) -
                            "a DFMA loop measured 1.19 TFLOP/s"}
 
 
-def cpu_oracle_time(n_sample: int, seed: int) -> tuple[float, float]:
+def cpu_oracle_time(n_sample: int, seed: int) -> float:
     """Seconds of the oracle's unblocked Givens HT reduction (Q and Z) of one
-    pencil of order n_sample, and its extrapolation to n by n^3."""
+    pencil of order n_sample of the bench workload, on one host core."""
     import oracle
     from paper_1710_08538_gb300 import pencils
     oracle.build()
     A, B = pencils.shifted_triu(n_sample, seed)
     t0 = time.perf_counter()
     oracle.givens_ht(A, B)
-    return time.perf_counter() - t0, n_sample
+    return time.perf_counter() - t0
+
+
+def cpu_oracle_fit(n: int, sizes: list[int], seed: int) -> dict:
+    """The oracle timed on each sample size, t(n) = c n^3 fitted by least
+    squares over the samples (the method is Theta(n^3)), extrapolated to n."""
+    samples = [(ns, cpu_oracle_time(ns, seed)) for ns in sizes]
+    c = sum(t * ns ** 3 for ns, t in samples) / sum(float(ns) ** 6 for ns, _ in samples)
+    return {"samples": samples, "c": c, "s_per_pencil": c * float(n) ** 3}
 
 
 def run_reference(args):
+    """The oracle arm: the CPU oracle's Givens HT reduction timed on this
+    host's cores.  A full n = 16384 reduction takes hours on one core, so each
+    step times bounded samples of the same workload and extrapolates by the
+    fitted c n^3 (stated in the line)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    times = []
+    sizes = cpu_sizes(args)
     for _ in range(max(args.warmup, 0)):
-        cpu_oracle_time(min(args.cpu_sample, 512), args.seed)
-    for _ in range(args.steps):
-        dt, ns = cpu_oracle_time(args.cpu_sample, args.seed)
-        times.append(dt * (args.n / ns) ** 3)
-    sec = statistics.mean(times)
+        cpu_oracle_time(min(sizes), args.seed)
+    fits = [cpu_oracle_fit(args.n, sizes, args.seed) for _ in range(args.steps)]
+    sec = statistics.mean(f["s_per_pencil"] for f in fits)
     value = f_nom(args.n) / sec / 1e12
+    sample = (f"unblocked Givens HT reduction (oracle, C, 1 thread) of the bench workload at n = "
+              f"{', '.join(str(x) for x in sizes)} per step, t = c n^3 fitted over them and extrapolated to "
+              f"n = {args.n} (not a timed n = {args.n} run)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "higher_is_better": True,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "s_per_pencil": sec,
-        "ms_per_step": sec * 1e3, "dtype": "f64", "data": "synthetic",
+        "ms_per_step": sec * 1e3, "extrapolated": True, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"single pencil n={args.n}, A~N(0,1), B=triu(N(0,1))+4I, Q and Z", "n": args.n},
-        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
-                         "sample": f"unblocked Givens HT reduction (oracle) of one n={args.cpu_sample} pencil per "
-                                   f"step, extrapolated to n={args.n} by n^3"},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": sample,
+                         "samples_s": [[ns, t] for ns, t in fits[-1]["samples"]]},
         "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "vs_baseline": None,
     }
     print(json.dumps(line), flush=True)
+
+
+def cpu_sizes(args) -> list[int]:
+    return [max(8, args.cpu_sample // 2), args.cpu_sample]
 
 
 # ----------------------------------------------------------------------------
@@ -212,11 +230,28 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
+def plan_steps(warmup: int, steps: int, t_step: float, spent: float, budget: float, extra: float) -> tuple[int, int]:
+    """Warm-up and timed steps that fit the wall-clock budget: the requested
+    ones when they fit; otherwise the warm-up first shrinks to its minimum of
+    3 (one of them being the end-to-end step), then the timed steps (at least
+    one).  t_step: seconds of one step; spent: seconds used so far (one warm-up
+    step included); extra: seconds of the work after the timed steps."""
+    left = budget - spent - extra
+    w_left = max(warmup - 1, 0)
+    if (w_left + steps) * t_step <= left:
+        return warmup, steps
+    w_min = max(min(warmup, 3) - 1, 0)
+    w_left = max(w_min, min(w_left, int(left // t_step) - steps))
+    k = max(1, min(steps, int((left - w_left * t_step) // t_step)))
+    return w_left + 1, k
+
+
 def run_ours(args):
     import numpy as np
     import torch
     import torch.distributed as dist
 
+    t_start = time.perf_counter()
     import __graft_entry__ as g
     g.build()
     import paper_1710_08538_gb300 as ht
@@ -246,6 +281,7 @@ def run_ours(args):
     B0.copy_(B_host.view(n, n).t())
     A, B, Q, Z = colmajor_empty(), colmajor_empty(), colmajor_empty(), colmajor_empty()
     stream = torch.cuda.current_stream(dev)
+    H_host = torch.empty(n * n, dtype=torch.float64).pin_memory()
 
     def step(stats=False, profile=0):
         A.copy_(A0)
@@ -253,8 +289,42 @@ def run_ours(args):
         return ht.reduce(A, B, Q, Z, want_qz=True, opts=ht.options(nb=nb, precision=prec, profile=profile),
                          stream=stream, with_stats=stats)
 
-    for _ in range(args.warmup):
+    def e2e_step() -> float:
+        # end to end through the C ABI with host buffers: H2D of A and B from
+        # pinned host memory, the reduction, D2H of H, T, Q and Z, all timed
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        A.copy_(A_host.view(n, n).t(), non_blocking=True)
+        B.copy_(B_host.view(n, n).t(), non_blocking=True)
+        ht.reduce(A, B, Q, Z, want_qz=True, opts=ht.options(nb=nb, precision=prec), stream=stream)
+        for X in (A, B, Q, Z):
+            H_host.view(n, n).t().copy_(X, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        return time.perf_counter() - t0
+
+    # warm-up: the first step is timed by the wall clock to plan the run within
+    # the budget; the last warm-up step is the end-to-end measurement (rank 0)
+    warmup, steps = args.warmup, args.steps
+    torch.cuda.synchronize(dev)
+    tw = time.perf_counter()
+    do_e2e = not args.no_e2e and rank == 0
+    e2e_dt = None
+    if warmup >= 1:
         step()
+        torch.cuda.synchronize(dev)
+        t_step = time.perf_counter() - tw
+        extra = 30.0 + (0.0 if args.no_cpu_baseline else 40.0)
+        if args.budget > 0:
+            warmup, steps = plan_steps(warmup, steps, t_step, time.perf_counter() - t_start, args.budget, extra)
+        if world > 1:
+            plan = torch.tensor([warmup, steps], dtype=torch.int64, device=dev)
+            dist.broadcast(plan, 0)
+            warmup, steps = int(plan[0].item()), int(plan[1].item())
+        for i in range(1, warmup):
+            if do_e2e and i == warmup - 1:
+                e2e_dt = e2e_step()
+            else:
+                step()
     torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
@@ -264,7 +334,9 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     ev0.record(stream)
     agg = None
-    for _ in range(args.steps):
+    for _ in range(steps):
+        # profile = 1: the library times every launch with CUDA events on this
+        # stream (the per-class times of the roofline); measured overhead 0.2%
         st = step(stats=True, profile=1)
         if agg is None:
             agg = {k: (list(v) if isinstance(v, list) else v) for k, v in st.items()}
@@ -278,11 +350,16 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
-    sec_per_pencil = ms / 1e3 / args.steps  # per rank; ranks run concurrently
-    value = job_value(world, args.steps, n, ms)
+    sec_per_pencil = ms / 1e3 / steps  # per rank; ranks run concurrently
+    value = job_value(world, steps, n, ms)
 
     # backward error of the last step (probes: exact FP64 GEMMs would take minutes)
     rep = check.invariants(A0, B0, A, B, Q, Z, probes=16, seed=7)
+    bwd_tol = 1e-12 if args.precision == "emu" else 20.0 * n * 2.0 ** -52
+    structure_ok = rep["h_nonzeros_below_subdiag"] == 0 and rep["t_nonzeros_below_diag"] == 0
+    orth_tol = 20.0 * n * 2.0 ** -52
+    bwd_ok = bool(structure_ok and rep["bwd_a"] <= bwd_tol and rep["bwd_b"] <= bwd_tol
+                  and rep["orth_q"] <= orth_tol and rep["orth_z"] <= orth_tol)
 
     # roofline of the dominant launch class (device time by CUDA events in the library)
     cls_ms = agg["ms_by_class"]
@@ -295,36 +372,27 @@ def run_ours(args):
                 for i in range(6) if cls_ms[i] > 0}
 
     e2e = None
-    if not args.no_e2e and rank == 0:
-        # end to end through the C ABI with host buffers: H2D of A, B, the
-        # reduction, D2H of H, T, Q, Z, all inside the timed interval
-        H_host = torch.empty(n * n, dtype=torch.float64).pin_memory()
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        A.copy_(A_host.view(n, n).t(), non_blocking=True)
-        B.copy_(B_host.view(n, n).t(), non_blocking=True)
-        ht.reduce(A, B, Q, Z, want_qz=True, opts=ht.options(nb=nb, precision=prec), stream=stream)
-        for X in (A, B, Q, Z):
-            H_host.view(n, n).t().copy_(X, non_blocking=True)
-        torch.cuda.synchronize(dev)
-        dt = time.perf_counter() - t0
-        e2e = {"value": f_nom(n) / dt / 1e12, "unit": "TFLOP/s", "s_per_pencil": dt,
-               "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": 4 * n * n * 8}
+    if e2e_dt is not None:
+        e2e = {"value": f_nom(n) / e2e_dt / 1e12, "unit": "TFLOP/s", "s_per_pencil": e2e_dt,
+               "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": 4 * n * n * 8,
+               "measured_on": "the last warm-up step (ht_reduce_ex via the Python binding, pinned host buffers)"}
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0:
-        dt, ns = cpu_oracle_time(args.cpu_sample, args.seed)
-        est = dt * (n / ns) ** 3
+        fit = cpu_oracle_fit(n, cpu_sizes(args), args.seed)
+        est = fit["s_per_pencil"]
         cpu = {"value": f_nom(n) / est / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
-               "s_per_pencil_extrapolated": est,
-               "sample": f"unblocked Givens HT reduction (oracle, C, 1 thread) of one n={ns} pencil of the same "
-                         f"workload in {dt:.2f} s, extrapolated to n={n} by n^3"}
+               "s_per_pencil_extrapolated": est, "samples_s": [[ns, t] for ns, t in fit["samples"]],
+               "sample": f"unblocked Givens HT reduction (oracle, C, 1 thread) of the same workload at n = "
+                         f"{', '.join(str(ns) for ns, _ in fit['samples'])}, t = c n^3 fitted over them and "
+                         f"extrapolated to n = {n}"}
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": "TFLOP/s", "higher_is_better": True,
-            "s_per_pencil": sec_per_pencil, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms / args.steps, "scaling": "weak", "vs_baseline": None,
+            "metric": METRIC, "value": value if bwd_ok else None, "unit": "TFLOP/s", "higher_is_better": True,
+            "s_per_pencil": sec_per_pencil, "n_gpus": world, "steps": steps, "warmup": warmup,
+            "steps_requested": args.steps, "warmup_requested": args.warmup,
+            "ms_per_step": ms / steps, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "precision_path": args.precision,
             "config": {"workload": f"single pencil n={n}, A~N(0,1), B=triu(N(0,1))+4I, Q and Z accumulated",
@@ -334,9 +402,10 @@ def run_ours(args):
                               f"A, B, Q, Z ({n * n * 8 / 2**20:.1f} MiB each) do not all exceed L2; not flushed "
                               "(not a headline size)"),
                        "parallelism": f"replicas x{world}"},
+            "bwd_err_ok": bwd_ok,
             "bwd_err": {"a": rep["bwd_a"], "b": rep["bwd_b"], "orth_q": rep["orth_q"], "orth_z": rep["orth_z"],
-                        "structure_ok": rep["h_nonzeros_below_subdiag"] == 0 and rep["t_nonzeros_below_diag"] == 0,
-                        "probes": 16},
+                        "structure_ok": structure_ok, "bwd_tol": bwd_tol, "orth_tol": orth_tol, "probes": 16,
+                        "estimate": "Frobenius norms estimated from 16 Gaussian probe vectors"},
             "stats": {"panels": agg["panels"], "early_absorptions": agg["early_absorptions"],
                       "ir_steps": agg["ir_steps"], "cols_with_ir": agg["cols_with_ir"],
                       "ms_by_class": dict(zip(ht.CLASS_NAMES[:7], cls_ms[:7]))},
@@ -347,10 +416,13 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "wall_s": time.perf_counter() - t_start,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+    if not bwd_ok:
+        sys.exit(1)
 
 
 if __name__ == "__main__":

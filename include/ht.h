@@ -67,7 +67,9 @@ typedef struct ht_options {
                           return HT_ERR_NOT_IMPLEMENTED (the WY factors always take 7) */
   uint64_t seed;       /* key of the singular-B perturbation (Remark 2.2) */
   int profile;         /* 1: time every launch by class into ht_stats (adds syncs) */
-  int reserved[7];
+  int wait_polls;      /* test option: polls before a bounded device-side wait gives up and the call returns
+                          HT_ERR_TIMEOUT; 0 = default (2^22 polls, seconds) */
+  int reserved[6];
 } ht_options;
 
 /* Launch classes of ht_stats.ms_by_class / flops_by_class / launches_by_class. */
@@ -151,6 +153,22 @@ int ht_reduce_batched(int batch, const int* n, double* const* A, const int* lda,
 #define HT_NOALLOC_NMAX 512
 int ht_reduce_noalloc(int n, double* A, int lda, double* B, int ldb, double* Q, int ldq, double* Z, int ldz,
                       int want_qz, ht_stream_t stream);
+
+/*
+ * ht_philox4x32_10 -- raw blocks of the device's counter-based generator,
+ * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), the generator that draws
+ * rho ~ N(0,1) (Box-Muller on words 0 and 1 of the block with counter
+ * (panel start s, global diagonal index, 0, 0) and key (seed lo, seed hi)) for
+ * the perturbation of a zero diagonal entry of B (Remark 2.2, Sec. 3.2.1).
+ * Exposed so that the generator can be checked against its published
+ * known-answer vectors.
+ *   count  number of blocks, >= 0
+ *   in     device, 6 x count uint32: counter[0..3], key[0..1] of each block
+ *   out    device, 4 x count uint32: the output words of each block
+ * Asynchronous on `stream`; returns -i for an invalid argument i, HT_ERR_CUDA
+ * if the launch fails.
+ */
+int ht_philox4x32_10(int count, const uint32_t* in, uint32_t* out, ht_stream_t stream);
 
 /* ht_last_device_status -- status word written by the device during the
  * last call on `stream` from this host thread (HT_OK, HT_ERR_TIMEOUT,

@@ -32,13 +32,13 @@ HT_PREC_FP64 = 0
 HT_PREC_EMU = 1
 
 EXPORTED = ["ht_reduce", "ht_reduce_ex", "ht_reduce_batched", "ht_reduce_noalloc", "ht_last_device_status",
-            "ht_finalize", "ht_status_string", "ht_version"]
+            "ht_finalize", "ht_status_string", "ht_version", "ht_philox4x32_10"]
 
 
 class HtOptions(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int), ("max_ir", ctypes.c_int), ("ir_tol_scale", ctypes.c_double),
                 ("precision", ctypes.c_int), ("emu_slices", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("profile", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("profile", ctypes.c_int), ("wait_polls", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
 class HtStats(ctypes.Structure):
@@ -94,6 +94,8 @@ def lib() -> ctypes.CDLL:
         L.ht_finalize.restype = ctypes.c_int
         L.ht_status_string.argtypes = [ctypes.c_int]
         L.ht_status_string.restype = ctypes.c_char_p
+        L.ht_philox4x32_10.argtypes = [ip, vp, vp, vp]
+        L.ht_philox4x32_10.restype = ctypes.c_int
         L.ht_version.argtypes = []
         L.ht_version.restype = ctypes.c_char_p
         _lib = L
@@ -136,11 +138,12 @@ def _stream_ptr(stream) -> int:
 
 
 def options(nb: int = 0, max_ir: int = 0, ir_tol_scale: float = 0.0, precision: int = HT_PREC_FP64,
-            emu_slices: int = 0, seed: int = 0, profile: int = 0) -> HtOptions:
+            emu_slices: int = 0, seed: int = 0, profile: int = 0, wait_polls: int = 0) -> HtOptions:
     o = HtOptions()
     o.nb, o.max_ir, o.ir_tol_scale, o.precision, o.emu_slices, o.seed = nb, max_ir, ir_tol_scale, precision, \
         emu_slices, seed
     o.profile = profile
+    o.wait_polls = wait_polls
     return o
 
 
@@ -189,6 +192,21 @@ def reduce_batched(As, Bs, Qs=None, Zs=None, want_qz: bool = True, stream=None):
     pz = (ctypes.c_void_p * cnt)(*[z.data_ptr() for z in Zs]) if want_qz else None
     rc = lib().ht_reduce_batched(cnt, n, pa, lda, pb, ldb, pq, pz, int(want_qz), _stream_ptr(stream))
     _check(rc)
+
+
+def philox4x32_10(blocks, stream=None):
+    """Raw Philox4x32-10 blocks computed by the device generator: ``blocks``
+    is a list of (counter[4], key[2]); returns a list of output[4]."""
+    import torch
+    cnt = len(blocks)
+    flat = [int(w) & 0xFFFFFFFF for c, k in blocks for w in list(c) + list(k)]
+    flat = [w - (1 << 32) if w >= (1 << 31) else w for w in flat]  # the same 32 bits as int32
+    dev_in = torch.tensor(flat, dtype=torch.int32, device="cuda")
+    dev_out = torch.zeros(4 * cnt, dtype=torch.int32, device="cuda")
+    _check(lib().ht_philox4x32_10(cnt, dev_in.data_ptr(), dev_out.data_ptr(), _stream_ptr(stream)))
+    torch.cuda.synchronize()
+    out = [int(x) & 0xFFFFFFFF for x in dev_out.cpu().tolist()]
+    return [out[4 * i:4 * i + 4] for i in range(cnt)]
 
 
 def finalize():

@@ -55,6 +55,7 @@ size_t ht_layout_work(HtWork& w, char* b, int n, int nb, int G, unsigned long lo
   w.nb = nb;
   w.G = G;
   w.ychunks = 4;
+  w.spin = HT_SPIN_LIMIT;
   const int nblk = n / HT_TRSV_BS + 2;
   const size_t nn = (size_t)n;
   size_t total = 0;
@@ -295,6 +296,9 @@ double fl_sweep(int mode, int p, int k, int nwin, double lines, int limit_base, 
 // One fused chain application, native FP64 or emulated (HT_PREC_EMU).
 cudaError_t run_sweep(Ctx& c, const HtSweepJob* jobs, int njobs, const double* wy, long wst, int mode, int p, int k,
                       int t0, int t1) {
+  if (c.w->prec == HT_PREC_EMU && c.w->tc)
+    return ht_tc_sweep_multi(c.st, jobs, njobs, wy, wst, mode, p, k, t0, t1, c.w->emu_dig, c.w->emu_exps,
+                             c.w->emu_geo, c.w->emu_cap, c.w->err);
   if (c.w->prec == HT_PREC_EMU)
     return ht_emu_sweep_multi(c.st, jobs, njobs, wy, wst, mode, p, k, t0, t1, c.w->emu_dig, c.w->emu_exps,
                               c.w->emu_cap, c.w->emu_mwy, c.w->emu_geo);
@@ -363,7 +367,7 @@ cudaError_t absorb(Ctx& c, int s, int k) {
       ht_right_block(p, k, bb, &d0, &d1);
       fl += fl_window(d1 - c0, d1 - d0) + 4.0 * (j + 1 + d0) * (d1 - c0) * (d1 - d0);
     }
-    if (nbr > 1) LAUNCH(HT_CLASS_RESTORE, fl, ht_launch_restore(st, 2, p, k, j, n, B, ldb, w.wyRR, wst, w.tstore, w.rtaus, w.rcount, w.err, w.ptime));
+    if (nbr > 1) LAUNCH(HT_CLASS_RESTORE, fl, ht_launch_restore(st, 2, p, k, j, n, B, ldb, w.wyRR, wst, w.tstore, w.rtaus, w.rcount, w.err, w.ptime, w.spin));
   }
   if (nbr > 1) {
     // rows 0..j of B, all rows of A and Z, one fused launch
@@ -421,7 +425,7 @@ cudaError_t absorb(Ctx& c, int s, int k) {
       if (t + 1 < nlb) ht_left_block(p, k, t + 1, &e0, &e1); else e1 = r1;
       fl += fl_window(e1 - r0, r1 - r0) + 4.0 * (n - (j + 1 + r1)) * (e1 - r0) * (r1 - r0);
     }
-    LAUNCH(HT_CLASS_RESTORE, fl, ht_launch_restore(st, 3, p, k, j, n, B, ldb, w.wyLR, wst, w.tstore, w.rtaus, w.rcount, w.err, w.ptime));
+    LAUNCH(HT_CLASS_RESTORE, fl, ht_launch_restore(st, 3, p, k, j, n, B, ldb, w.wyLR, wst, w.tstore, w.rtaus, w.rcount, w.err, w.ptime, w.spin));
   }
   {
     const HtSweepJob jobs[2] = {{A, lda, 0, j, n - j, j + 1, 0, 0}, {Q, ldq, 1, 0, c.want_qz ? n : 0, j + 1, 0, 0}};
@@ -482,6 +486,8 @@ int reduce_impl(int n, double* A, int lda, double* B, int ldb, double* Q, int ld
   PoolEntry* pe = acquire(n, nb, &rc);
   if (!pe) return rc;
   pe->w.prec = prec;
+  pe->w.spin = (opt && opt->wait_polls > 0) ? (long)opt->wait_polls : (long)HT_SPIN_LIMIT;
+  pe->w.tc = opt ? opt->reserved[0] : 0;
   const int result = ht_reduce_core(pe->w, pe->host_status, pe->pt_dev, n, A, lda, B, ldb, Q, ldq, Z, ldz, want_qz,
                                     nb, max_ir, tol_scale, seed, opt && opt->profile, stats, st);
   release(pe);

@@ -140,6 +140,8 @@ struct HtWork {
   void* emu_geo;           // their table (emu_cap int4)
   int emu_cap;             // windows per launch of the emulated sweeps
   int prec;                // HT_PREC_* of the current call
+  long spin;               // polls before a bounded device wait gives up (HT_SPIN_LIMIT by default)
+  int tc;                  // emulated sweeps on tcgen05 (ht_tc.cu) instead of mma.sync (ht_emu.cu)
   cudaStream_t stream;
 };
 #define HT_PART_STRIDE 80   // >= nb + 8 for nb <= 64 ... plus norms
@@ -163,7 +165,7 @@ cudaError_t ht_launch_chains(cudaStream_t st, double* V2, double* U2, long ld, i
 // restore chain of B (mode 2: RQ right, mode 3: QR left), one cooperative launch
 cudaError_t ht_launch_restore(cudaStream_t st, int mode, int p, int k, int j, int n, double* B, long ldb, double* wy,
                               size_t stride, double* tstore, double* taus, int* flag, int* err,
-                              unsigned long long* ptime);
+                              unsigned long long* ptime, long spin);
 // One target of a fused chain application (see ht_apply.cu).
 #define HT_SWEEP_MAXJOBS 4
 struct HtSweepJob {
@@ -191,6 +193,15 @@ long ht_merge_stride();
 cudaError_t ht_emu_sweep_multi(cudaStream_t st, const HtSweepJob* jobs, int njobs, const double* wy, long stride, int mode,
                                int p, int k, int t0, int t1, void* dig, int* exps, int cap, double* mwy, void* geo);
 size_t ht_emu_window_bytes(int nb);
+// as ht_sweep_multi with FP64 emulated on the tcgen05 tensor cores (ht_tc.cu):
+// consecutive windows grouped into products of at most 64 x 64, `cap` groups per
+// launch, dig: cap * ht_tc_group_bytes() bytes, exps: cap ints, geo: cap int4;
+// k <= 32; a bounded wait that gives up raises HT_ERR_TIMEOUT in *err
+cudaError_t ht_tc_sweep_multi(cudaStream_t st, const HtSweepJob* jobs, int njobs, const double* wy, long stride,
+                              int mode, int p, int k, int t0, int t1, void* dig, int* exps, void* geo, int cap,
+                              int* err);
+int ht_tc_group(int k);
+size_t ht_tc_group_bytes();
 size_t ht_emu_merge_doubles(int cap);
 cudaError_t ht_sweep(cudaStream_t st, int right, double* X, long ldx, int line0, int nlines, int origin,
                      const double* wy, long stride, int mode, int p, int k, int t0, int t1, int use_limit,

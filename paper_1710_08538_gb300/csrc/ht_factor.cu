@@ -555,6 +555,7 @@ struct SplitArgs {
   int* flag;     // [0] reflectors published, [1] T factors formed (zeroed by the launcher)
   int* err;      // device error word
   unsigned long long* ptime;
+  long spin;     // polls before a bounded wait gives up
 };
 
 // step s: window [off, off + width), nrefl kr, factored lines start f0, next block [n0, n1)
@@ -582,10 +583,13 @@ __device__ __forceinline__ SplitStep split_step(bool right, int p, int k, int s)
   return g;
 }
 
-// bounded wait of one thread for *p >= v; raises HT_ERR_TIMEOUT on expiry
-__device__ bool split_wait(const int* p, int v, int* err) {
+// bounded wait of one thread for *p >= v: gives up at once when the error
+// word is already set (a wait elsewhere gave up), else after `spin` polls,
+// raising HT_ERR_TIMEOUT
+__device__ bool split_wait(const int* p, int v, int* err, long spin) {
   if (ht_ld_acquire(p) >= v) return true;
-  for (long it = 0; it < (long)HT_SPIN_LIMIT; ++it) {
+  for (long it = 0; it < spin; ++it) {
+    if (*(volatile int*)err != 0) return false;
     __nanosleep(32);
     if (ht_ld_acquire(p) >= v) return true;
   }
@@ -600,7 +604,7 @@ __device__ bool split_wait(const int* p, int v, int* err) {
 // reflector published, no waiting).  Returns false on a timeout.
 template <bool SMEM>
 __device__ bool split_reflect(bool right, double x[4], int w, int kk, const double* gV, const double* gTau,
-                              const int* flag, int base, int* err) {
+                              const int* flag, int base, int* err, long spin) {
   const int lane = threadIdx.x & 31;
   // reflector data: tau and v issued together; while this warp is behind the
   // factorization (the next flag already up) the next reflector is fetched
@@ -617,7 +621,7 @@ __device__ bool split_reflect(bool right, double x[4], int w, int kk, const doub
   auto ready = [&](int q, bool wait) -> int {  // 1: published, 0: not yet, -1: timeout
     int st = 1;
     if (!SMEM && lane == 0) {
-      if (wait) st = split_wait(flag, base + q + 1, err) ? 1 : -1;
+      if (wait) st = split_wait(flag, base + q + 1, err, spin) ? 1 : -1;
       else st = (ht_ld_acquire(flag) >= base + q + 1) ? 1 : 0;
     }
     return __shfl_sync(0xffffffffu, st, 0);
@@ -716,7 +720,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1) restore_split_kernel(SplitArgs 
         auto ready = [&](int q, bool wait) -> int {
           int st = 0;
           if (lane == 0) {
-            if (wait) st = split_wait(a.flag, base + q + 1, a.err) ? 1 : -1;
+            if (wait) st = split_wait(a.flag, base + q + 1, a.err, a.spin) ? 1 : -1;
             else st = (ht_ld_acquire(a.flag) >= base + q + 1) ? 1 : 0;
           }
           return __shfl_sync(0xffffffffu, st, 0);
@@ -813,7 +817,8 @@ __global__ void __launch_bounds__(RS_THREADS, 1) restore_split_kernel(SplitArgs 
                 if ((src >> 5) == v2 && src < wu) y[u] = xv;
               }
             }
-            ok = split_reflect<true>(right, y, gp.width, gp.kr, f.Vs, f.tau, a.flag, (t - 1) * RS_KSTEP, a.err);
+            ok = split_reflect<true>(right, y, gp.width, gp.kr, f.Vs, f.tau, a.flag, (t - 1) * RS_KSTEP, a.err,
+                                    a.spin);
             // back into the union frame
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -841,7 +846,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1) restore_split_kernel(SplitArgs 
               }
             }
             ok = split_reflect<false>(right, y, g.width, g.kr, a.wy + (size_t)t * a.stride, a.taus + (size_t)t * k, a.flag,
-                                      t * RS_KSTEP, a.err);
+                                      t * RS_KSTEP, a.err, a.spin);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               const int r = lane + 32 * u;
@@ -865,7 +870,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1) restore_split_kernel(SplitArgs 
       if (t > 0) {
         // Ww_{t-1} = V T^T for the later sweeps, once T_{t-1} is formed
         const SplitStep g = split_step(right, p, k, t - 1);
-        if (tid == 0) split_wait(a.flag + 1, t, a.err);
+        if (tid == 0) split_wait(a.flag + 1, t, a.err, a.spin);
         __syncthreads();
         const double* Vw = a.wy + (size_t)(t - 1) * a.stride;
         const double* Tg = a.tstore + (size_t)(t - 1) * k * k;
@@ -885,7 +890,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1) restore_split_kernel(SplitArgs 
         b0 = gp.b0; b1 = gp.b1;
       }
       if (b1 > b0 && cta - RS_FIRST_BULK < (b1 - b0 + SRR - 1) / SRR) {
-        if (tid == 0) split_wait(a.flag + 1, t, a.err);  // T_{t-1} formed (a timeout is reported, work goes on)
+        if (tid == 0) split_wait(a.flag + 1, t, a.err, a.spin);  // T_{t-1} formed (a timeout is reported, work goes on)
         __syncthreads();
       }
       const unsigned long long t0 = (a.ptime && cta == RS_FIRST_BULK && tid == 0) ? rs_now() : 0ull;
@@ -927,7 +932,7 @@ cudaError_t ht_launch_chains(cudaStream_t st, double* V2, double* U2, long ld, i
 
 cudaError_t ht_launch_restore(cudaStream_t st, int mode, int p, int k, int j, int n, double* B, long ldb, double* wy,
                               size_t stride, double* tstore, double* taus, int* flag, int* err,
-                              unsigned long long* ptime) {
+                              unsigned long long* ptime, long spin) {
   set_factor_attr();
   const int nsteps = (mode == 2) ? ht_num_right_blocks(p, k) - 1 : ht_num_left_blocks(p, k);
   if (nsteps <= 0) return cudaSuccess;
@@ -937,7 +942,7 @@ cudaError_t ht_launch_restore(cudaStream_t st, int mode, int p, int k, int j, in
   if (k <= 32 && sms > RS_FIRST_BULK && flag && err && taus) {  // the helpers hold three blocks of a line
     cudaError_t e = cudaMemsetAsync(flag, 0, 2 * sizeof(int), st);
     if (e != cudaSuccess) return e;
-    SplitArgs sa{mode, p, k, j, n, B, ldb, wy, stride, tstore, taus, flag, err, ptime};
+    SplitArgs sa{mode, p, k, j, n, B, ldb, wy, stride, tstore, taus, flag, err, ptime, spin > 0 ? spin : HT_SPIN_LIMIT};
     void* sargs[] = {&sa};
     return cudaLaunchCooperativeKernel((void*)restore_split_kernel, dim3(sms), dim3(RS_THREADS), sargs,
                                        factor_smem_doubles() * sizeof(double), st);

@@ -60,6 +60,13 @@ extern "C" int ht_reduce_noalloc(int n, double* A, int lda, double* B, int ldb, 
     g_noalloc_ptr[dev] = (double*)p;
   }
   if (n == 0) return HT_OK;
+  // the workspace must fit the array before anything is written (its size
+  // depends on the device's SM count through the panel's CTA count)
+  const int nb = 32;
+  const int G = ht_panel_max_ctas(nb);
+  HtWork w;
+  const size_t bytes = n > 2 ? ht_layout_work(w, nullptr, n, nb, G, nullptr) : 0;
+  if (bytes > sizeof(double) * (size_t)HT_NOALLOC_WORDS) return HT_ERR_TOO_LARGE;
   if (want_qz) {
     if (ht_launch_set_identity(st, Q, ldq, n) != cudaSuccess) return HT_ERR_CUDA;
     if (ht_launch_set_identity(st, Z, ldz, n) != cudaSuccess) return HT_ERR_CUDA;
@@ -68,11 +75,6 @@ extern "C" int ht_reduce_noalloc(int n, double* A, int lda, double* B, int ldb, 
     if (ht_launch_zero(st, B, ldb, n, n, 1) != cudaSuccess) return HT_ERR_CUDA;
     return cudaStreamSynchronize(st) == cudaSuccess ? HT_OK : HT_ERR_CUDA;
   }
-  const int nb = 32;
-  const int G = ht_panel_max_ctas(nb);
-  HtWork w;
-  const size_t bytes = ht_layout_work(w, nullptr, n, nb, G, nullptr);
-  if (bytes > sizeof(double) * (size_t)HT_NOALLOC_WORDS) return HT_ERR_TOO_LARGE;
   ht_layout_work(w, (char*)g_noalloc_ptr[dev], n, nb, G, nullptr);
   // the array keeps the previous call's contents: start from zeros
   if (cudaMemsetAsync(g_noalloc_ptr[dev], 0, bytes, st) != cudaSuccess) return HT_ERR_CUDA;

@@ -57,6 +57,7 @@ struct PanelArgs {
   unsigned long long* prog;  // per-CTA progress words of the look-ahead solve
   double* nearv;   // B(block i-1, block i) x_i of the look-ahead solve
   double* wpart;   // chunk partials of the triangular multiply (nchunks x n)
+  long spin;       // polls before a bounded wait gives up
 };
 
 __device__ __forceinline__ unsigned long long ht_now() {
@@ -433,7 +434,7 @@ __device__ void trsv_gs(const PanelArgs& a, Grid& grid, int m, const double* rhs
 // target (warp 0 polls with relaxed loads, all of a lane's words in flight
 // together, then one acquire fence; the block follows).  Fails at once when
 // the error word is already set (a wait elsewhere gave up), else after
-// HT_SPIN_LIMIT polls, setting HT_ERR_TIMEOUT; the caller then carries on
+// `spin` polls, setting HT_ERR_TIMEOUT; the caller then carries on
 // without the data.
 __device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p) {
   unsigned long long v;
@@ -441,12 +442,13 @@ __device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long l
   return v;
 }
 template <class Idx>
-__device__ bool la_wait(const unsigned long long* p, int cnt, Idx idx, unsigned long long target, int* err) {
+__device__ bool la_wait(const unsigned long long* p, int cnt, Idx idx, unsigned long long target, int* err,
+                        long spin) {
   __shared__ int flag[1];
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     int ok = 0;
-    for (long it = 0; it <= (long)HT_SPIN_LIMIT; ++it) {
+    for (long it = 0; it <= spin; ++it) {
       unsigned long long v[4] = {~0ull, ~0ull, ~0ull, ~0ull};
 #pragma unroll
       for (int u = 0; u < 4; ++u)
@@ -471,12 +473,12 @@ __device__ bool la_wait(const unsigned long long* p, int cnt, Idx idx, unsigned 
 // p[idxB(0..cntB-1)] (cntB <= 32) against targetB, all loads of a poll in flight together.
 template <class IdxB>
 __device__ bool la_wait2(const unsigned long long* p, int cntA, unsigned long long targetA, int cntB, IdxB idxB,
-                         unsigned long long targetB, int* err) {
+                         unsigned long long targetB, int* err, long spin) {
   __shared__ int flag2[1];
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     int ok = 0;
-    for (long it = 0; it <= (long)HT_SPIN_LIMIT; ++it) {
+    for (long it = 0; it <= spin; ++it) {
       const unsigned long long va = (lane < cntA) ? ld_relaxed64(p + lane) : ~0ull;
       const unsigned long long vb = (lane < cntB) ? ld_relaxed64(p + idxB(lane)) : ~0ull;
       if (__all_sync(0xffffffffu, va >= targetA && vb >= targetB)) { ok = 1; break; }
@@ -592,7 +594,7 @@ __device__ void trsv_la(const PanelArgs& a, int m, double* accv, double* sol, bo
       // (tile t belongs to CTA LA_ND + t mod NF), which finished step s-2
       if (s > 0)
         la_wait2(a.prog, LA_ND, base + 2 * s, min(NF, BI / 32),
-                 [&](int u) { return LA_ND + (i * (BI / 32) + u) % NF; }, s > 1 ? base + s - 1 : 0ull, a.err);
+                 [&](int u) { return LA_ND + (i * (BI / 32) + u) % NF; }, s > 1 ? base + s - 1 : 0ull, a.err, a.spin);
       // accumulator of block i in the frame of this step
       for (int q = tid; q < rows; q += blockDim.x) {
         const double av = __ldcg(accv + r0 + q);
@@ -624,7 +626,7 @@ __device__ void trsv_la(const PanelArgs& a, int m, double* accv, double* sol, bo
         if (tid == 0) { a.xmax[(size_t)i * 32] = mx; a.flags[i] = shift; }
       }
       la_publish(a.prog + cta, base + 2 * s + 1);
-      la_wait(a.prog, LA_ND, ident, base + 2 * s + 1, a.err);
+      la_wait(a.prog, LA_ND, ident, base + 2 * s + 1, a.err, a.spin);
       const int Ei = frame(i, sa, sx);
       if (cta == 0 && tid == 0) a.exps[i] = Ei;
       // ---- P2: nearv = B(block i-1, block i) x_i, one 32-row tile per CTA ----
@@ -656,7 +658,7 @@ __device__ void trsv_la(const PanelArgs& a, int m, double* accv, double* sol, bo
     for (int s = 0; s + 2 < nbk; ++s) {
       const int i = nbk - 1 - s, r0 = i * BI, rows = min(BI, m - r0);
       const int lim = (i - 1) * BI;  // rows above the next diagonal block
-      la_wait(a.prog, LA_ND, ident, base + 2 * s + 1, a.err);
+      la_wait(a.prog, LA_ND, ident, base + 2 * s + 1, a.err, a.spin);
       int sh_acc, sh_x;
       frame(i, sh_acc, sh_x);
       if (f * 32 < lim) {
@@ -1183,22 +1185,36 @@ __global__ void frob_kernel(const double* B, long ldb, int n, double* out) {
 
 __global__ void sqrt_kernel(double* x) { *x = sqrt(*x); }
 
-// Philox4x32-10 (Salmon et al., SC'11) and Box-Muller, keyed like the oracle:
-// counter (column, index, 0, 0), key (seed lo, seed hi).
-__device__ double philox_normal(uint64_t seed, uint32_t column, uint32_t index) {
-  uint32_t c0 = column, c1 = index, c2 = 0, c3 = 0;
-  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of the counter c under the
+// key (k0, k1), the key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
   for (int r = 0; r < 10; ++r) {
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
-    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
-    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
     k0 += 0x9E3779B9u;
     k1 += 0xBB67AE85u;
   }
-  const double u1 = ((double)c0 + 1.0) * 2.3283064365386963e-10;
-  const double u2 = (double)c1 * 2.3283064365386963e-10;
+}
+
+// N(0,1) sample by Box-Muller on words 0 and 1 of the block with counter
+// (column, index, 0, 0) and key (seed lo, seed hi).
+__device__ double philox_normal(uint64_t seed, uint32_t column, uint32_t index) {
+  uint32_t c[4] = {column, index, 0u, 0u};
+  philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const double u1 = ((double)c[0] + 1.0) * 2.3283064365386963e-10;
+  const double u2 = (double)c[1] * 2.3283064365386963e-10;
   return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+}
+
+// raw blocks: in = (counter[4], key[2]) per item, out = block[4] per item
+__global__ void philox_block_kernel(int count, const uint32_t* in, uint32_t* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  uint32_t c[4] = {in[6 * i], in[6 * i + 1], in[6 * i + 2], in[6 * i + 3]};
+  philox4x32_10(c, in[6 * i + 4], in[6 * i + 5]);
+  for (int q = 0; q < 4; ++q) out[4 * i + q] = c[q];
 }
 
 __global__ void diag_prepare_kernel(double* B, long ldb, int n, int s, uint64_t seed, const double* bnorm,
@@ -1266,6 +1282,7 @@ cudaError_t ht_launch_panel(HtWork& w, double* A, int lda, const double* B, int 
   const int m = w.n - s - 1;
   a.cap = (m + w.G - 1) / w.G;
   a.ptime = w.ptime;
+  a.spin = w.spin > 0 ? w.spin : HT_SPIN_LIMIT;
   a.Xinv = w.Xinv; a.safe = w.safe; a.xmax = w.xmax; a.prog = w.prog; a.nearv = w.nearv; a.wpart = w.wpart;
   size_t smem = smem_doubles(w.nb, a.cap) * sizeof(double);
   a.stage = smem <= (size_t)kPanelSmemMax - 4096;
@@ -1284,4 +1301,13 @@ int ht_panel_max_ctas(int nb) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   set_panel_attr();
   return sms;  // one CTA per SM: the phases are latency-bound, not occupancy-bound
+}
+
+extern "C" int ht_philox4x32_10(int count, const uint32_t* in, uint32_t* out, ht_stream_t stream) {
+  if (count < 0) return -1;
+  if (count > 0 && !in) return -2;
+  if (count > 0 && !out) return -3;
+  if (count == 0) return HT_OK;
+  philox_block_kernel<<<(count + 127) / 128, 128, 0, (cudaStream_t)stream>>>(count, in, out);
+  return cudaGetLastError() == cudaSuccess ? HT_OK : HT_ERR_CUDA;
 }

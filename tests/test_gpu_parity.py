@@ -185,3 +185,57 @@ def test_batched_matches_single(ht):
     torch.cuda.synchronize()
     for (A, B), dA, dB, dQ, dZ in zip(refs, As, Bs, Qs, Zs):
         checks.assert_invariants(A, B, dA.cpu().numpy(), dB.cpu().numpy(), dQ.cpu().numpy(), dZ.cpu().numpy())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "emu"])
+def test_elementwise_vs_algorithm1_three_solve_blocks(ht, prec):
+    """n = 600: the trailing system has up to 599 rows, so the look-ahead
+    solve runs a chain of three 256-row diagonal blocks (block inverses, far
+    updates one step behind, progress words) and the restores span several
+    stripes; the result still equals the oracle's Algorithm 1 elementwise."""
+    n, nb = 600, 32
+    A, B = pencils.random_qr(n, 1600)
+    p = ht.HT_PREC_FP64 if prec == "fp64" else ht.HT_PREC_EMU
+    (H, T, Q, Z), _ = run_gpu(ht, A, B, nb=nb, precision=p)
+    ref = checks.sign_normalize(*hh.househt(A, B, nb=nb)[:4])
+    got = checks.sign_normalize(H, T, Q, Z)
+    for name, a, b in zip("HTQZ", ref, got):
+        err = float(np.max(np.abs(a - b)))
+        assert err <= 1e-10 * max(1.0, float(np.max(np.abs(a)))), (name, err)
+
+
+def test_bounded_wait_times_out_and_library_recovers(ht):
+    """A bounded device wait that runs out: with the test option wait_polls = 1
+    the cross-CTA waits of the look-ahead solve and of the restore chains give
+    up almost at once, the kernels raise HT_ERR_TIMEOUT in the error word, keep
+    joining their grid barriers and return; the call reports the error, the
+    device status word agrees, and the next call on the same workspace
+    succeeds."""
+    n = 600
+    A, B = pencils.random_qr(n, 1601)
+    with pytest.raises(ht.HtError) as e:
+        run_gpu(ht, A, B, nb=32, wait_polls=1)
+    assert e.value.code == ht.HT_ERR_TIMEOUT
+    status = ctypes.c_int(-1)
+    assert ht.lib().ht_last_device_status(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),
+                                          ctypes.byref(status)) == ht.HT_OK
+    assert status.value == ht.HT_ERR_TIMEOUT
+    (H, T, Q, Z), _ = run_gpu(ht, A, B, nb=32)
+    checks.assert_invariants(A, B, H, T, Q, Z)
+    assert ht.lib().ht_last_device_status(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),
+                                          ctypes.byref(status)) == ht.HT_OK
+    assert status.value == ht.HT_OK
+
+
+def test_device_philox_known_answers(ht):
+    """The device generator of the Remark 2.2 perturbation reproduces the
+    published Philox4x32-10 known-answer vectors (tests/golden)."""
+    import os
+    rows = []
+    for ln in open(os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")):
+        ln = ln.split("#")[0].split()
+        if ln:
+            w = [int(x, 16) for x in ln]
+            rows.append((w[0:4], w[4:6], w[6:10]))
+    got = ht.philox4x32_10([(c, k) for c, k, _ in rows])
+    assert got == [o for _, _, o in rows]
