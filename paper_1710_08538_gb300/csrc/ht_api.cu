@@ -93,6 +93,7 @@ size_t ht_layout_work(HtWork& w, char* b, int n, int nb, int G, unsigned long lo
   // merged windows of the emulated sweeps of chains with k <= 16
   const size_t oEmuM = take(ht_emu_merge_doubles(w.emu_cap));
   const size_t oEmuG = take(2 * (size_t)w.emu_cap);  // int4 = 2 doubles
+  const size_t oCf = take((size_t)n + 8);  // 2 (n + 8) ints
   const size_t oRc = take(2);
   const size_t oRt = take(nn + 2 * HT_NB_MAX);
   if (!b) return total;
@@ -129,6 +130,7 @@ size_t ht_layout_work(HtWork& w, char* b, int n, int nb, int G, unsigned long lo
   w.emu_mwy = (double*)(b + oEmuM);
   w.emu_geo = (void*)(b + oEmuG);
   w.rcount = (int*)(b + oRc);
+  w.cflags = (int*)(b + oCf);
   w.rtaus = (double*)(b + oRt);
   w.wpart = (double*)(b + oWpart);
   w.tstore = (double*)(b + oTst);
@@ -307,6 +309,73 @@ cudaError_t run_sweep(Ctx& c, const HtSweepJob* jobs, int njobs, const double* w
   return ht_sweep_multi(c.st, jobs, njobs, wy, wst, mode, p, k, t0, t1);
 }
 
+// Restore chain on B (mode 2: RQ, Sec. 3.3.1e; mode 3: QR, Sec. 3.3.2f), fl
+// flops in all.  seg: in segments of RS_SEG steps, each launch updating only
+// the lines its own steps need, followed by an emulated sweep of the
+// segment's transforms on the remaining lines of B (rows 0 .. j as well for
+// the RQ chain); otherwise one launch.
+constexpr int RS_SEG = 32;
+// flops of restore steps [ta, tb) whose updates reach the lines [blo, bhi): the
+// factorization of each block and its transform on the trailing lines of B
+double fl_restore(int mode, int p, int k, int ta, int tb, int blo, int bhi) {
+  double f = 0.0;
+  for (int t = ta; t < tb; ++t) {
+    int w, kr, lim;
+    if (mode == 2) {
+      const int bb = ht_num_right_blocks(p, k) - 1 - t;
+      int c0, c1, d0, d1;
+      ht_right_block(p, k, bb - 1, &c0, &c1);
+      ht_right_block(p, k, bb, &d0, &d1);
+      w = d1 - c0; kr = d1 - d0; lim = d0;
+      f += fl_window(w, kr) + 4.0 * std::max(0, lim - blo) * w * kr;
+    } else {
+      const int nlb = ht_num_left_blocks(p, k);
+      int r0, r1, e0, e1;
+      ht_left_block(p, k, t, &r0, &r1);
+      if (t + 1 < nlb) ht_left_block(p, k, t + 1, &e0, &e1); else e1 = r1;
+      w = e1 - r0; kr = r1 - r0; lim = r1;
+      f += fl_window(w, kr) + 4.0 * std::max(0, bhi - lim) * w * kr;
+    }
+  }
+  return f;
+}
+
+cudaError_t restore_chain(Ctx& c, int mode, int p, int k, int j, double* wy, long wst, bool seg) {
+  HtWork& w = *c.w;
+  const int nsteps = ht_restore_steps(mode, p, k);
+  if (nsteps <= 0) return cudaSuccess;
+  const double* wyc = wy;
+  if (!seg) {
+    LAUNCH(HT_CLASS_RESTORE, fl_restore(mode, p, k, 0, nsteps, 0, p),
+           ht_launch_restore(c.st, mode, p, k, j, c.n, c.B, c.ldb, wy, wst, w.tstore, w.rtaus, w.rcount, w.err,
+                             w.ptime, w.spin));
+    return cudaSuccess;
+  }
+  for (int ta = 0; ta < nsteps; ta += RS_SEG) {
+    const int tb = std::min(nsteps, ta + RS_SEG);
+    int blo0 = 0, bhi0 = p;
+    if (tb < nsteps) ht_restore_band(mode, p, k, tb, &blo0, &bhi0);
+    LAUNCH(HT_CLASS_RESTORE, fl_restore(mode, p, k, ta, tb, blo0, bhi0),
+           ht_launch_restore(c.st, mode, p, k, j, c.n, c.B, c.ldb, wy, wst, w.tstore, w.rtaus, w.rcount, w.err,
+                             w.ptime, w.spin, ta, tb));
+    int blo = 0, bhi = p;
+    if (tb < nsteps) ht_restore_band(mode, p, k, tb, &blo, &bhi);
+    if (mode == 2) {
+      // rows 0 .. j + blo of B: rows above the segment's band, including rows 0 .. j
+      // (only those for the last segment, blo = 0)
+      const HtSweepJob job = {c.B, c.ldb, 1, 0, j + 1 + blo, j + 1, 0, 0};
+      LAUNCH(HT_CLASS_SWEEP, fl_sweep(2, p, k, tb, j + 1 + blo, -1, false) - fl_sweep(2, p, k, ta, j + 1 + blo, -1, false),
+             run_sweep(c, &job, 1, wyc, wst, 2, p, k, ta, tb));
+    } else if (mode == 3 && bhi < p) {
+      // columns j + 1 + bhi .. n - 1 of B, right of the segment's band
+      const HtSweepJob job = {c.B, c.ldb, 0, j + 1 + bhi, p - bhi, j + 1, 0, 0};
+      LAUNCH(HT_CLASS_SWEEP, fl_sweep(3, p, k, tb, p - bhi, -1, true) - fl_sweep(3, p, k, ta, p - bhi, -1, true),
+             run_sweep(c, &job, 1, wyc, wst, 3, p, k, ta, tb));
+    }
+  }
+  return cudaSuccess;
+}
+
 // Absorption of k right and k left reflectors (Sec. 3.3.1 and 3.3.2).
 cudaError_t absorb(Ctx& c, int s, int k) {
   HtWork& w = *c.w;
@@ -338,8 +407,13 @@ cudaError_t absorb(Ctx& c, int s, int k) {
   LAUNCH(HT_CLASS_OTHER, 0.0,
          cudaMemcpy2DAsync(w.U2w, n * sizeof(double), U + k, n * sizeof(double), p * sizeof(double), k,
                            cudaMemcpyDeviceToDevice, st));
-  LAUNCH(HT_CLASS_CHAIN_FACTOR, 2.0 * fl_chain(p, k),
-         ht_launch_chains(st, V + k, w.U2w, n, p, k, w.wyR, w.wyL, wst, w.L1, w.R1));
+  if (k <= 32)
+    LAUNCH(HT_CLASS_CHAIN_FACTOR, 2.0 * fl_chain(p, k),
+           ht_launch_chains_wave(st, V + k, w.U2w, n, p, k, w.wyR, w.wyL, wst, w.L1, w.R1, w.tmp1, w.tmp3, w.cflags,
+                                 w.err, w.spin));
+  else
+    LAUNCH(HT_CLASS_CHAIN_FACTOR, 2.0 * fl_chain(p, k),
+           ht_launch_chains(st, V + k, w.U2w, n, p, k, w.wyR, w.wyL, wst, w.L1, w.R1));
   // (c)-(e) step 1: A, Z, B columns j+1..n-1 times the chain, one fused launch
   {
     const HtSweepJob jobs[3] = {{A, lda, 1, 0, n, j + 1, 0, 0},
@@ -356,25 +430,19 @@ cudaError_t absorb(Ctx& c, int s, int k) {
     LAUNCH(HT_CLASS_RANKK, fl_rk, ht_launch_rankk_right(st, Z, ldz, n, s + 1, n - k, k, V, n, w.L1, k, w.T, nb));
   LAUNCH(HT_CLASS_GEMM, fl_gemm(n, k, k),
          ht_gemm(st, 'N', 'T', n, k, k, -1.0, w.Y, n, w.L1, k, 1.0, A + (size_t)(n - k) * lda, lda));
-  // partial restore: RQ chain bottom to top (Sec. 3.3.1e), one cooperative launch
+  // partial restore: RQ chain bottom to top (Sec. 3.3.1e); on the emulated path in
+  // segments, each followed by the segment's transforms on the rows above its band
+  // (emulated sweep) instead of FP64 updates inside the restore kernel
   const int nbr = ht_num_right_blocks(p, k);
-  {
-    double fl = 0.0;
-    for (int t = 0; t + 1 < nbr; ++t) {
-      const int bb = nbr - 1 - t;
-      int c0, c1, d0, d1;
-      ht_right_block(p, k, bb - 1, &c0, &c1);
-      ht_right_block(p, k, bb, &d0, &d1);
-      fl += fl_window(d1 - c0, d1 - d0) + 4.0 * (j + 1 + d0) * (d1 - c0) * (d1 - d0);
-    }
-    if (nbr > 1) LAUNCH(HT_CLASS_RESTORE, fl, ht_launch_restore(st, 2, p, k, j, n, B, ldb, w.wyRR, wst, w.tstore, w.rtaus, w.rcount, w.err, w.ptime, w.spin));
-  }
+  const bool seg = w.prec == HT_PREC_EMU && k <= 32;
+  if (nbr > 1) CK(restore_chain(c, 2, p, k, j, w.wyRR, wst, seg));
   if (nbr > 1) {
-    // rows 0..j of B, all rows of A and Z, one fused launch
+    // rows 0..j of B (on the emulated path already done with the segments),
+    // all rows of A and Z, one fused launch
     const HtSweepJob jobs[3] = {{A, lda, 1, 0, n, j + 1, 0, 0},
                                 {Z, ldz, 1, 0, c.want_qz ? n : 0, j + 1, 0, 0},
-                                {B, ldb, 1, 0, j + 1, j + 1, 0, 0}};
-    const double fl = fl_sweep(2, p, k, nbr - 1, j + 1, -1, false) +
+                                {B, ldb, 1, 0, seg ? 0 : j + 1, j + 1, 0, 0}};
+    const double fl = (seg ? 0.0 : fl_sweep(2, p, k, nbr - 1, j + 1, -1, false)) +
                       (c.want_qz ? 2.0 : 1.0) * fl_sweep(2, p, k, nbr - 1, n, -1, false);
     LAUNCH(HT_CLASS_SWEEP, fl, run_sweep(c, jobs, 3, w.wyRR, wst, 2, p, k, 0, nbr - 1));
   }
@@ -415,18 +483,9 @@ cudaError_t absorb(Ctx& c, int s, int k) {
   LAUNCH(HT_CLASS_RANKK, fl_rkl * (n - j), ht_rankk_left(st, A, lda, j, n - j, s + 1, 2 * k, k, Ut, 2 * k, w.S, nb));
   if (c.want_qz)
     LAUNCH(HT_CLASS_RANKK, fl_rkl * dn, ht_rankk_right_w(st, Q, ldq, n, s + 1, 2 * k, k, Ut, 2 * k, w.S, nb));
-  // (f) restore: QR chain top to bottom, one cooperative launch
+  // (f) restore: QR chain top to bottom (in segments on the emulated path)
   const int nlb = ht_num_left_blocks(p, k);
-  {
-    double fl = 0.0;
-    for (int t = 0; t < nlb; ++t) {
-      int r0, r1, e0, e1;
-      ht_left_block(p, k, t, &r0, &r1);
-      if (t + 1 < nlb) ht_left_block(p, k, t + 1, &e0, &e1); else e1 = r1;
-      fl += fl_window(e1 - r0, r1 - r0) + 4.0 * (n - (j + 1 + r1)) * (e1 - r0) * (r1 - r0);
-    }
-    LAUNCH(HT_CLASS_RESTORE, fl, ht_launch_restore(st, 3, p, k, j, n, B, ldb, w.wyLR, wst, w.tstore, w.rtaus, w.rcount, w.err, w.ptime, w.spin));
-  }
+  CK(restore_chain(c, 3, p, k, j, w.wyLR, wst, seg));
   {
     const HtSweepJob jobs[2] = {{A, lda, 0, j, n - j, j + 1, 0, 0}, {Q, ldq, 1, 0, c.want_qz ? n : 0, j + 1, 0, 0}};
     const double fl = fl_sweep(3, p, k, nlb, n - j, -1, true) +
@@ -487,7 +546,7 @@ int reduce_impl(int n, double* A, int lda, double* B, int ldb, double* Q, int ld
   if (!pe) return rc;
   pe->w.prec = prec;
   pe->w.spin = (opt && opt->wait_polls > 0) ? (long)opt->wait_polls : (long)HT_SPIN_LIMIT;
-  pe->w.tc = opt ? opt->reserved[0] : 0;
+  pe->w.tc = (opt && opt->reserved[0]) ? 0 : 1;
   const int result = ht_reduce_core(pe->w, pe->host_status, pe->pt_dev, n, A, lda, B, ldb, Q, ldq, Z, ldz, want_qz,
                                     nb, max_ir, tol_scale, seed, opt && opt->profile, stats, st);
   release(pe);

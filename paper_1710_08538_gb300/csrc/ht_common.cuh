@@ -142,6 +142,7 @@ struct HtWork {
   int prec;                // HT_PREC_* of the current call
   long spin;               // polls before a bounded device wait gives up (HT_SPIN_LIMIT by default)
   int tc;                  // emulated sweeps on tcgen05 (ht_tc.cu) instead of mma.sync (ht_emu.cu)
+  int* cflags;             // wavefront chains: columns published per window (2 (n + 8) ints)
   cudaStream_t stream;
 };
 #define HT_PART_STRIDE 80   // >= nb + 8 for nb <= 64 ... plus norms
@@ -162,10 +163,21 @@ cudaError_t ht_gemm_ws(cudaStream_t st, char ta, char tb, int M, int N, int K, d
 // QL chain of V2 and QR chain of U2 (two CTAs) plus the T / Ww formation of every window
 cudaError_t ht_launch_chains(cudaStream_t st, double* V2, double* U2, long ld, int p, int k, double* wyR, double* wyL,
                              size_t stride, double* L1, double* R1);
+// the same two chains as a wavefront over their windows (ht_chain.cu, k <= 32):
+// pubR, pubL hold p k doubles each, flags 2 (p / k + 2) ints; then T / Ww
+cudaError_t ht_launch_chains_wave(cudaStream_t st, double* V2, double* U2, long ld, int p, int k, double* wyR,
+                                  double* wyL, size_t stride, double* L1, double* R1, double* pubR, double* pubL,
+                                  int* flags, int* err, long spin);
+cudaError_t ht_launch_form_wy(cudaStream_t st, double* wyR, double* wyL, size_t stride, int p, int k);
 // restore chain of B (mode 2: RQ right, mode 3: QR left), one cooperative launch
+// steps [ta, tb) of it (tb < 0: to the end); a launch that ends before the last
+// step leaves the lines outside ht_restore_band(tb) to a later sweep
 cudaError_t ht_launch_restore(cudaStream_t st, int mode, int p, int k, int j, int n, double* B, long ldb, double* wy,
                               size_t stride, double* tstore, double* taus, int* flag, int* err,
-                              unsigned long long* ptime, long spin);
+                              unsigned long long* ptime, long spin, int ta = 0, int tb = -1);
+int ht_restore_steps(int mode, int p, int k);
+// lines [blo, bhi) (relative to j + 1) that the steps up to tb - 1 still update themselves
+void ht_restore_band(int mode, int p, int k, int tb, int* blo, int* bhi);
 // One target of a fused chain application (see ht_apply.cu).
 #define HT_SWEEP_MAXJOBS 4
 struct HtSweepJob {

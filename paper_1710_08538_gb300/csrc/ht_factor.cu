@@ -28,26 +28,33 @@ namespace {
 constexpr int MAXW = 2 * HT_NB_MAX;  // largest window height
 
 // Householder scalars of a column with pivot x0 and squared tail norm tail
-// (DLARFG rule): beta = (alpha - x0) / alpha, alpha = -sign(x0) ||x||,
-// scal = 1 / (x0 - alpha).
-// Called by lanes 0 and 1 of one warp: both quotients come out of one division
-// sequence (lane 0: beta = (alpha - x0) / alpha, lane 1: scal = 1 / (x0 - alpha)).
+// (DLARFG rule): alpha = -sign(x0) ||x||, beta = (alpha - x0) / alpha,
+// scal = 1 / (x0 - alpha).  With r = 1 / ||x|| (one reciprocal square root),
+// beta = 1 + |x0| r; only scal takes a division.  Called by lanes 0 and 1 of
+// one warp (lane 0: beta and alpha, lane 1: scal); the chain of dependent FP64
+// operations is the critical path of the factorizations.
 __device__ __forceinline__ void house_scalars(double x0, double tail, double* sc, int lane) {
   if (tail == 0.0) {
     if (lane == 0) { sc[0] = 0.0; sc[1] = x0; sc[2] = 0.0; }
     return;
   }
-  const double nr = sqrt(x0 * x0 + tail);
+  const double s2 = x0 * x0 + tail;
+  const double r = rsqrt(s2);
+  const double nr = s2 * r;
   const double alpha = (x0 >= 0.0) ? -nr : nr;
-  const double q = (lane == 0 ? alpha - x0 : 1.0) / (lane == 0 ? alpha : x0 - alpha);
-  if (lane == 0) { sc[0] = q; sc[1] = alpha; }
-  else sc[2] = q;
+  if (lane == 0) { sc[0] = fma(fabs(x0), r, 1.0); sc[1] = alpha; }
+  else sc[2] = 1.0 / (x0 - alpha);
 }
 
 // Householder QR (ql = false) or QL (ql = true) of the w x kk column-major
 // matrix X (shared, ld w) in place.  On return X holds R (upper triangle in
 // rows 0..kk-1) or L (lower triangle in rows w-kk..w-1) with exact zeros
 // elsewhere, Vs (w x kk) the reflector vectors in product order and tau[q].
+// Warp roles: warp 0 carries the critical path (next column, its norm and
+// scalars); the FP64 unit of an SM is shared by its four sub-partitions and a
+// busy warp on warp 0's own sub-partition slows warp 0's dependent chain the
+// most, so the trailing columns go to the warps of sub-partitions 1-3 only
+// (warps 1-3, 5-7); warp 4 publishes the reflectors when asked to.
 // Look-ahead: warp 0 updates only the next column to reduce and prepares its
 // reflector scalars (double-buffered in sc) while warps 1.. update the other
 // columns four at a time with a packed cross-lane reduction.  bv (w entries)
@@ -83,7 +90,8 @@ struct HousePub {
 __device__ void house_factor(double* X, int w, int kk, bool ql, double* Vs, double* tau, double* sc, double* bv,
                              const HousePub* pub = nullptr) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int nw = (blockDim.x >> 5) - (pub ? 1 : 0);  // warps that take part in the factorization
+  const bool bulk = (wid & 3) != 0 && wid < 8;       // trailing-column warps (sub-partitions 1-3)
+  const int br = wid - 1 - (wid >> 2), nbulk = 6;    // their rank
   for (int e = tid; e < w * kk; e += blockDim.x) Vs[e] = 0.0;
   if (wid == 0) {
     const int c = ql ? kk - 1 : 0, t = ql ? w - kk + c : c;
@@ -109,7 +117,7 @@ __device__ void house_factor(double* X, int w, int kk, bool ql, double* Vs, doub
     }
     if (tid == 0) tau[q] = beta;
     __syncthreads();
-    if (pub && wid == nw) {
+    if (pub && wid == 4) {
       // publisher warp: reflector q to global memory, then its flag
       for (int r = lane; r < w; r += 32) pub->gV[r + (size_t)q * w] = Vs[r + q * w];
       if (lane == 0) pub->gTau[q] = tau[q];
@@ -140,8 +148,8 @@ __device__ void house_factor(double* X, int w, int kk, bool ql, double* Vs, doub
         __syncwarp();
         if (lane < 2) house_scalars(X[t2 + cnext * w], sq, nxt, lane);
       }
-    } else if (beta != 0.0) {
-      for (int g0 = cb + 4 * (wid - 1); g0 < ce; g0 += 4 * (nw - 1)) {
+    } else if (bulk && beta != 0.0) {
+      for (int g0 = cb + 4 * br; g0 < ce; g0 += 4 * nbulk) {
         double d[4] = {0.0, 0.0, 0.0, 0.0};
         for (int r = lo + lane; r < hi; r += 32) {
           const double vr = Vs[r + q * w];
@@ -556,6 +564,8 @@ struct SplitArgs {
   int* err;      // device error word
   unsigned long long* ptime;
   long spin;     // polls before a bounded wait gives up
+  int ta, tb;    // steps of this launch (a segment of the chain)
+  int blo, bhi;  // lines the bulk CTAs update: [blo, bhi) (relative to j + 1)
 };
 
 // step s: window [off, off + width), nrefl kr, factored lines start f0, next block [n0, n1)
@@ -563,7 +573,7 @@ struct SplitArgs {
 struct SplitStep {
   int off, width, kr, f0, n0, n1, b0, b1;
 };
-__device__ __forceinline__ SplitStep split_step(bool right, int p, int k, int s) {
+__host__ __device__ __forceinline__ SplitStep split_step(bool right, int p, int k, int s) {
   SplitStep g;
   if (right) {
     const int bb = ht_num_right_blocks(p, k) - 1 - s;
@@ -670,10 +680,11 @@ __global__ void __launch_bounds__(RS_THREADS, 1) restore_split_kernel(SplitArgs 
   const int nsteps = right ? ht_num_right_blocks(p, k) - 1 : ht_num_left_blocks(p, k);
   const int cta = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   double* Bt = a.B + (size_t)j1 + (size_t)j1 * a.ldb;
-  for (int t = 0; t <= nsteps; ++t) {
+  const int ta = a.ta, tb = min(a.tb, nsteps);
+  for (int t = ta; t <= tb; ++t) {
     if (cta == 0) {
       // ---- factorization of step t, reflectors published as they form ----
-      if (t < nsteps) {
+      if (t < tb) {
         const SplitStep g = split_step(right, p, k, t);
         const int w = g.width, kr = g.kr;
         for (int e = tid; e < w * kr; e += blockDim.x) {
@@ -694,7 +705,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1) restore_split_kernel(SplitArgs 
       }
     } else if (cta == 1) {
       const unsigned long long t0 = (a.ptime && tid == 0) ? rs_now() : 0ull;
-      if (t > 0) {
+      if (t > ta) {
         // T_{t-1} from the Gram matrix, tau and V of step t-1 kept in shared memory, then Ww_{t-1}
         const SplitStep g = split_step(right, p, k, t - 1);
         const int kr = g.kr;
@@ -707,7 +718,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1) restore_split_kernel(SplitArgs 
         __syncthreads();
         if (tid == 0) ht_st_release(a.flag + 1, t);
       }
-      if (t < nsteps) {
+      if (t < tb) {
         // Gram columns of step t as the reflectors arrive, without block barriers:
         // warp wi keeps the columns c = wi (mod nw) in shared memory and, for every
         // arriving v_q (fetched by each warp itself, the next one early when its
@@ -774,14 +785,16 @@ __global__ void __launch_bounds__(RS_THREADS, 1) restore_split_kernel(SplitArgs 
       }
       if (a.ptime && tid == 0) a.ptime[17] += rs_now() - t0;
     } else if (cta < 2 + RS_HELP) {
-      // ---- helpers: the next block of step t takes G_{t-1}, then G_t as it streams ----
-      if (t < nsteps) {
+      // ---- helpers: the next block of step t takes G_{t-1} (already applied at a
+      // segment's first step, by the previous segment), then G_t as it streams ----
+      if (t < tb) {
         const unsigned long long t0 = (a.ptime && cta == 2 && tid == 0) ? rs_now() : 0ull;
         const SplitStep g = split_step(right, p, k, t);
         const int nl = g.n1 - g.n0, per = (nl + RS_HELP - 1) / RS_HELP;
         const int l0 = g.n0 + (cta - 2) * per, l1 = min(g.n1, l0 + per);
-        const SplitStep gp = split_step(right, p, k, t > 0 ? t - 1 : 0);
-        if (t > 0 && l1 > l0) {
+        const bool prev = t > ta;
+        const SplitStep gp = split_step(right, p, k, prev ? t - 1 : t);
+        if (prev && l1 > l0) {
           // the reflectors of step t-1 (all published) from shared memory
           const double* Vp = a.wy + (size_t)(t - 1) * a.stride;
           for (int e = tid; e < gp.width * gp.kr; e += blockDim.x) f.Vs[e] = __ldcg(Vp + e);
@@ -793,7 +806,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1) restore_split_kernel(SplitArgs 
           // the line over the union of both windows: right [off_t, off_t + width_t) holds both
           // transforms' columns (step t-1 acts on [off_{t-1}, ...) which is inside); left likewise
           const int lo = min(g.off, gp.off), hi = max(g.off + g.width, gp.off + gp.width);
-          const int wu = (t > 0) ? hi - lo : g.width, ou = (t > 0) ? lo : g.off;
+          const int wu = prev ? hi - lo : g.width, ou = prev ? lo : g.off;
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int r = lane + 32 * u;
@@ -802,7 +815,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1) restore_split_kernel(SplitArgs 
                             : 0.0;
           }
           bool ok = true;
-          if (t > 0) {
+          if (prev) {
             // G_{t-1} acts on rows [gp.off - ou, ...) of x: shift into its own frame
             double y[4];
             const int sh = gp.off - ou;
@@ -867,7 +880,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1) restore_split_kernel(SplitArgs 
         if (a.ptime && cta == 2 && tid == 0) a.ptime[18] += rs_now() - t0;
       }
     } else if (cta == RS_WCTA) {
-      if (t > 0) {
+      if (t > ta) {
         // Ww_{t-1} = V T^T for the later sweeps, once T_{t-1} is formed
         const SplitStep g = split_step(right, p, k, t - 1);
         if (tid == 0) split_wait(a.flag + 1, t, a.err, a.spin);
@@ -879,16 +892,19 @@ __global__ void __launch_bounds__(RS_THREADS, 1) restore_split_kernel(SplitArgs 
         __syncthreads();
         form_w(f.Vs, f.Tm, g.width, g.kr, a.wy + (size_t)(t - 1) * a.stride + a.stride / 2);
       }
-    } else if (t > 0) {
-      // ---- bulk: G_{t-1} with T_{t-1} beyond step t's next block (step t-1's at the end) ----
+    } else if (t > ta) {
+      // ---- bulk: G_{t-1} with T_{t-1} beyond step t's next block (step t-1's at the
+      // end), within the lines [blo, bhi) of this segment ----
       const SplitStep gp = split_step(right, p, k, t - 1);
       int b0, b1;
-      if (t < nsteps) {
+      if (t < tb) {
         const SplitStep g = split_step(right, p, k, t);
         b0 = g.b0; b1 = g.b1;
       } else {
         b0 = gp.b0; b1 = gp.b1;
       }
+      b0 = max(b0, a.blo);
+      b1 = min(b1, a.bhi);
       if (b1 > b0 && cta - RS_FIRST_BULK < (b1 - b0 + SRR - 1) / SRR) {
         if (tid == 0) split_wait(a.flag + 1, t, a.err, a.spin);  // T_{t-1} formed (a timeout is reported, work goes on)
         __syncthreads();
@@ -899,7 +915,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1) restore_split_kernel(SplitArgs 
                (int)gridDim.x - RS_FIRST_BULK);
       if (a.ptime && cta == RS_FIRST_BULK && tid == 0) a.ptime[19] += rs_now() - t0;
     }
-    if (t == nsteps) break;
+    if (t == tb) break;
     __threadfence();
     grid.sync();
   }
@@ -930,19 +946,44 @@ cudaError_t ht_launch_chains(cudaStream_t st, double* V2, double* U2, long ld, i
   return cudaGetLastError();
 }
 
+cudaError_t ht_launch_form_wy(cudaStream_t st, double* wyR, double* wyL, size_t stride, int p, int k) {
+  set_factor_attr();
+  const int nw = ht_num_windows(p, k);
+  form_wy_kernel<<<2 * nw, HT_THREADS, factor_smem_doubles() * sizeof(double), st>>>(wyR, wyL, stride, p, k, nw, nw);
+  return cudaGetLastError();
+}
+
+int ht_restore_steps(int mode, int p, int k) {
+  return (mode == 2) ? ht_num_right_blocks(p, k) - 1 : ht_num_left_blocks(p, k);
+}
+
+void ht_restore_band(int mode, int p, int k, int tb, int* blo, int* bhi) {
+  // lines beyond the next block of step tb - 1: the ones a segment ending at
+  // tb does not need (rows above for the RQ restore, columns right for the QR one)
+  const SplitStep g = split_step(mode == 2, p, k, tb - 1);
+  *blo = (mode == 2) ? g.b1 : 0;
+  *bhi = (mode == 2) ? p : g.b0;
+}
+
 cudaError_t ht_launch_restore(cudaStream_t st, int mode, int p, int k, int j, int n, double* B, long ldb, double* wy,
                               size_t stride, double* tstore, double* taus, int* flag, int* err,
-                              unsigned long long* ptime, long spin) {
+                              unsigned long long* ptime, long spin, int ta, int tb) {
   set_factor_attr();
-  const int nsteps = (mode == 2) ? ht_num_right_blocks(p, k) - 1 : ht_num_left_blocks(p, k);
+  const int nsteps = ht_restore_steps(mode, p, k);
   if (nsteps <= 0) return cudaSuccess;
+  if (tb < 0 || tb > nsteps) tb = nsteps;
+  if (ta < 0) ta = 0;
+  if (ta >= tb) return cudaSuccess;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (k <= 32 && sms > RS_FIRST_BULK && flag && err && taus) {  // the helpers hold three blocks of a line
     cudaError_t e = cudaMemsetAsync(flag, 0, 2 * sizeof(int), st);
     if (e != cudaSuccess) return e;
-    SplitArgs sa{mode, p, k, j, n, B, ldb, wy, stride, tstore, taus, flag, err, ptime, spin > 0 ? spin : HT_SPIN_LIMIT};
+    int blo = 0, bhi = p;
+    if (tb < nsteps) ht_restore_band(mode, p, k, tb, &blo, &bhi);
+    SplitArgs sa{mode, p, k, j, n, B, ldb, wy, stride, tstore, taus, flag, err, ptime, spin > 0 ? spin : HT_SPIN_LIMIT,
+                 ta, tb, blo, bhi};
     void* sargs[] = {&sa};
     return cudaLaunchCooperativeKernel((void*)restore_split_kernel, dim3(sms), dim3(RS_THREADS), sargs,
                                        factor_smem_doubles() * sizeof(double), st);

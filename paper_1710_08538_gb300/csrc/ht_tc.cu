@@ -47,7 +47,7 @@ namespace {
 
 constexpr int TM = 128;                 // lines per CTA (tensor-memory lanes)
 constexpr int TW = 64;                  // largest window width (K and N of the product)
-constexpr int TTHREADS = 256;           // 8 warps: two per lane quarter
+constexpr int TTHREADS = 512;           // 16 warps: four per lane quarter, 16 columns of a line each
 constexpr int NDX = 6, NDG = 7;         // digits of a line / of G
 constexpr int XS = TW + 1;              // leading dimension of the FP64 stripe (odd)
 constexpr int XD_PLANE = TM * TW * 2;   // bytes of one digit plane of the lines (K-major core matrices)
@@ -58,7 +58,7 @@ constexpr int OFF_XD = 0;
 constexpr int OFF_GD = OFF_XD + NDX * XD_PLANE;
 constexpr int OFF_XF = OFF_GD + GD_BYTES;
 constexpr int OFF_MISC = OFF_XF + XF_BYTES;
-constexpr int MISC_BYTES = 2048;        // barriers, tensor-memory address, line bounds, abort flag
+constexpr int MISC_BYTES = 4096;        // barriers, tensor-memory address, line bounds, abort flag
 constexpr int SMEM_BYTES = OFF_MISC + MISC_BYTES + 1024;  // + slack to align the base to 1024 bytes
 static_assert(SMEM_BYTES <= 232448, "shared memory of one CTA");
 constexpr int PREP_SMEM = (TW * TW + TW * 32) * 8;  // G and G(:, window) Vw
@@ -66,17 +66,11 @@ constexpr int TMEM_COLS = 512;
 constexpr long TC_POLLS = 1L << 24;     // bounded mbarrier waits
 
 // digit pairs (a, b) (0-based: a of the line, b of G), grouped per accumulator
-// in level order; 10 groups, at most 4 pairs each, of one level each
-struct Pair { int a, b; };
-__constant__ Pair c_pairs[27] = {
-    {0, 0},                                   // g0  L2
-    {0, 1}, {1, 0},                           // g1  L3
-    {0, 2}, {1, 1}, {2, 0},                   // g2  L4
-    {0, 3}, {1, 2}, {2, 1}, {3, 0},           // g3  L5
-    {0, 4}, {1, 3}, {2, 2}, {3, 1}, {4, 0},   // g4, g5  L6
-    {0, 5}, {1, 4}, {2, 3}, {3, 2}, {4, 1}, {5, 0},   // g6, g7  L7
-    {0, 6}, {1, 5}, {2, 4}, {3, 3}, {4, 2}, {5, 1}};  // g8, g9  L8
-__constant__ int c_gstart[11] = {0, 1, 3, 6, 10, 14, 15, 19, 21, 25, 27};
+// in level order; 10 groups, at most 4 pairs each, of one level each:
+//   g0 L2: (0,0) | g1 L3: (0,1) (1,0) | g2 L4: (0,2) (1,1) (2,0)
+//   g3 L5: (0,3) (1,2) (2,1) (3,0) | g4, g5 L6: (0,4) (1,3) (2,2) (3,1); (4,0)
+//   g6, g7 L7: (0,5) (1,4) (2,3) (3,2); (4,1) (5,0)
+//   g8, g9 L8: (0,6) (1,5) (2,4) (3,3); (4,2) (5,1)
 constexpr int NGROUP = 10;
 
 // ---------------------------------------------------------------------------
@@ -165,18 +159,29 @@ __device__ __forceinline__ uint32_t unbias2(uint32_t lo, uint32_t hi) {
   return b.u;
 }
 
-// byte offset of element (row, col) of a K-major operand tile without swizzle:
-// core matrices of 8 rows x 16 bytes, K-adjacent ones 128 bytes apart,
-// row groups (8 rows) 1024 bytes apart (K = 64 per row group)
+// byte offset of element (row, k) of a K-major operand tile without swizzle,
+// core matrices of 8 rows x 16 bytes: the row groups of one 8-column K chunk
+// are contiguous (stride 128 bytes), so the tensor core reads along M without
+// bank conflicts; K chunks are rows / 8 * 128 bytes apart
+template <int ROWS>
 __host__ __device__ __forceinline__ int kmajor_off(int row, int kcol) {
-  return (row >> 3) * 1024 + (kcol >> 3) * 128 + (row & 7) * 16 + (kcol & 7) * 2;
+  return (kcol >> 3) * (ROWS * 16) + (row >> 3) * 128 + (row & 7) * 16 + (kcol & 7) * 2;
 }
 
 // exact integer from an FP32 accumulator that holds one (|c| <= 2^24)
 __device__ __forceinline__ int f2i(uint32_t u) { return __float2int_rn(__uint_as_float(u)); }
 
-// int64 -> double times 2^ex without FP64 arithmetic (round to nearest even);
-// the rare results outside the normal range take the FP64 route
+// results below the normal range: the mantissa shifted into a subnormal (or
+// zero), above it an infinity (neither the sweep's inputs nor G produce one)
+__device__ __noinline__ unsigned long long scaled_tiny(unsigned long long sgn, unsigned long long mant, int be) {
+  if (be > 2046) return sgn | (0x7ffull << 52);
+  const int sh = 1 - be;
+  if (sh > 53) return sgn;
+  return sgn | ((mant + (1ull << (sh - 1))) >> sh);
+}
+
+// int64 -> double times 2^ex in integer arithmetic (round to nearest even):
+// GB300 issues FP64 instructions at 1/64 of its integer rate
 __device__ __forceinline__ double scaled_double(long long t, int ex) {
   if (t == 0) return 0.0;
   const unsigned long long sgn = (unsigned long long)t & 0x8000000000000000ull;
@@ -196,7 +201,7 @@ __device__ __forceinline__ double scaled_double(long long t, int ex) {
   const int be = e2 + 1023;
   if (be >= 1 && be <= 2046)
     return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | (mant & 0xFFFFFFFFFFFFFull)));
-  return ldexp((double)t, ex);
+  return __longlong_as_double((long long)scaled_tiny(sgn, mant, be));
 }
 
 // ---------------------------------------------------------------------------
@@ -204,11 +209,12 @@ __device__ __forceinline__ double scaled_double(long long t, int ex) {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
-  // start address, leading byte offset 128 (K-adjacent core matrices), stride
-  // byte offset 1024 (8-row groups), descriptor version 1, no swizzle
-  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         (1ull << 46);
+// shared-memory matrix descriptor: start address, leading byte offset (between
+// K-adjacent core matrices), stride byte offset (between 8-row groups),
+// descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
 }
 
 // kind::f16, D = F32, A = B = F16, both K-major, N = 32, M = 128
@@ -252,15 +258,20 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                "l"(src), "r"(bytes), "r"(bar)
                : "memory");
 }
+// 8-byte asynchronous copy global -> shared (no register round trip, all in flight together)
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
+}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t ta, uint32_t r[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(ta));
+__device__ __forceinline__ void tmem_ld8(uint32_t ta, uint32_t r[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(ta));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -324,14 +335,14 @@ __global__ void __launch_bounds__(TTHREADS) tc_prep_kernel(const double* wy, lon
   atomicMax(&fmax, em);
   __syncthreads();
   const int F = fmax;
-  // digits: element (r = K, c = N) of plane b at byte kmajor_off(c, r)
+  // digits: element (r = K, c = N) of plane b at byte kmajor_off<TW>(c, r)
   uint16_t* out = dig + (size_t)blockIdx.x * (GD_BYTES / 2);
   for (int e = tid; e < TW * TW; e += blockDim.x) {
     const int r = e % TW, c = e / TW;
     const double v = (r < wu && c < wu) ? G[r + c * TW] : 0.0;
     uint32_t h[NDG];
     digit_bits<NDG>(to_fixed<1>(v, F), h);
-    const int off = kmajor_off(c, r) >> 1;
+    const int off = kmajor_off<TW>(c, r) >> 1;
 #pragma unroll
     for (int b = 0; b < NDG; ++b) {
       union { uint16_t u; __half x; } cv;
@@ -372,6 +383,42 @@ __device__ __forceinline__ uint32_t acc_col(int h, int gi) {
   return h == 0 ? 32u * gi : (gi < 6 ? 320u + 32u * gi : 32u * (gi - 6));
 }
 
+// The pair table: a, b of pair i, and the first pair of group g (kGs(10) = 27).
+__host__ __device__ constexpr int kPa(int i) {
+  constexpr int t[27] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 5, 0, 1, 2, 3, 4, 5};
+  return t[i];
+}
+__host__ __device__ constexpr int kPb(int i) {
+  constexpr int t[27] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 5, 4, 3, 2, 1, 0, 6, 5, 4, 3, 2, 1};
+  return t[i];
+}
+__host__ __device__ constexpr int kGs(int i) {
+  constexpr int t[11] = {0, 1, 3, 6, 10, 14, 15, 19, 21, 25, 27};
+  return t[i];
+}
+
+// MMAs of accumulator groups [G0, G1) of output half H, interleaved across the
+// groups (slot s of every group, then slot s + 1) so that consecutive MMAs go to
+// different accumulators; slot s of a group is its pair s / 4 at k-step s % 4.
+// Fully unrolled: every descriptor is a base descriptor plus a constant (the
+// start-address field takes byte offsets / 16 and does not overflow here).
+template <int H, int G0, int G1>
+__device__ __forceinline__ void issue_groups(uint32_t tbase, uint64_t da, uint64_t db) {
+#pragma unroll
+  for (int s = 0; s < 16; ++s) {
+#pragma unroll
+    for (int gi = G0; gi < G1; ++gi) {
+      const int pi = kGs(gi) + (s >> 2);
+      if (pi < kGs(gi + 1)) {
+        const int ks = s & 3;
+        const uint32_t col = H == 0 ? 32u * gi : (gi < 6 ? 320u + 32u * gi : 32u * (gi - 6));
+        mma_f16(tbase + col, da + (uint64_t)((kPa(pi) * XD_PLANE + ks * 2 * (TM * 16)) >> 4),
+                db + (uint64_t)((kPb(pi) * GD_PLANE + 4 * H * 128 + ks * 2 * (TW * 16)) >> 4), s > 0 ? 1u : 0u);
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(TTHREADS, 1) tc_sweep_kernel(TcBatch b) {
   extern __shared__ __align__(1024) unsigned char tsm_raw[];
   unsigned char* tsm = (unsigned char*)(((uintptr_t)tsm_raw + 1023) & ~(uintptr_t)1023);
@@ -380,8 +427,8 @@ __global__ void __launch_bounds__(TTHREADS, 1) tc_sweep_kernel(TcBatch b) {
   double* Xf = (double*)(tsm + OFF_XF);
   uint64_t* bars = (uint64_t*)(tsm + OFF_MISC);  // 0: G copy, 1: MMA half 0, 2: half 1a, 3: half 1b, 4: free
   uint32_t* tslot = (uint32_t*)(bars + 8);
-  int* Es = (int*)(bars + 16);                   // 2 x TM line bounds
-  volatile int* abort_flag = (volatile int*)(Es + 2 * TM);
+  int* Es = (int*)(bars + 16);                   // 4 x TM partial line bounds
+  volatile int* abort_flag = (volatile int*)(Es + 4 * TM);
 
   TcJob jb = b.job[0];
 #pragma unroll
@@ -391,8 +438,8 @@ __global__ void __launch_bounds__(TTHREADS, 1) tc_sweep_kernel(TcBatch b) {
   const int lines = min(TM, jb.line0 + jb.nlines - lb);
   if (lines <= 0) return;  // uniform over the CTA, before any barrier or allocation
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int quarter = warp & 3, hh = warp >> 2;
-  const int li = 32 * quarter + lane;  // this thread's line (tensor-memory lane)
+  const int quarter = warp & 3, cq = warp >> 2;
+  const int li = 32 * quarter + lane;  // this thread's line (tensor-memory lane); cq: its column quarter
   double* X = jb.X;
   const long ldx = jb.ldx;
   const uint32_t bar_g = smem_u32(bars + 0), bar_m0 = smem_u32(bars + 1), bar_m1 = smem_u32(bars + 2),
@@ -443,32 +490,35 @@ __global__ void __launch_bounds__(TTHREADS, 1) tc_sweep_kernel(TcBatch b) {
     if (jb.right) {
       for (int e = tid; e < TM * TW; e += TTHREADS) {
         const int l = e % TM, c = e / TM;
-        Xf[l * XS + c] = (l < lines && c < w) ? X[(size_t)(lb + l) + (size_t)(o0 + c) * ldx] : 0.0;
+        if (l < lines && c < w) cp_async8(Xf + l * XS + c, X + (size_t)(lb + l) + (size_t)(o0 + c) * ldx);
+        else Xf[l * XS + c] = 0.0;
       }
     } else {
       for (int e = tid; e < TM * TW; e += TTHREADS) {
         const int c = e % TW, l = e / TW;
-        Xf[l * XS + c] = (l < lines && c < w) ? X[(size_t)(o0 + c) + (size_t)(lb + l) * ldx] : 0.0;
+        if (l < lines && c < w) cp_async8(Xf + l * XS + c, X + (size_t)(o0 + c) + (size_t)(lb + l) * ldx);
+        else Xf[l * XS + c] = 0.0;
       }
     }
+    cp_async_wait_all();
     __syncthreads();
-    // ---- per-line bound over the window, from both halves of the line ----
-    const int c0 = 32 * hh;
+    // ---- per-line bound over the window, from the four quarters of the line ----
+    const int c0 = 16 * cq;
     {
       int em = 1;
 #pragma unroll 8
-      for (int c = 0; c < 32; ++c) em = max(em, expo(Xf[li * XS + c0 + c]));
-      Es[hh * TM + li] = em;
+      for (int c = 0; c < 16; ++c) em = max(em, expo(Xf[li * XS + c0 + c]));
+      Es[cq * TM + li] = em;
     }
     __syncthreads();
-    const int E = max(Es[li], Es[TM + li]);
-    // ---- digits of this thread's 32 columns -> the A operand planes ----
+    const int E = max(max(Es[li], Es[TM + li]), max(Es[2 * TM + li], Es[3 * TM + li]));
+    // ---- digits of this thread's 16 columns -> the A operand planes ----
 #pragma unroll 1
-    for (int ch = 0; ch < 4; ++ch) {
+    for (int ch = 0; ch < 2; ++ch) {
       uint32_t hb[8][NDX];
 #pragma unroll
       for (int i = 0; i < 8; ++i) digit_bits<NDX>(to_fixed<0>(Xf[li * XS + c0 + 8 * ch + i], E), hb[i]);
-      const int boff = kmajor_off(li, c0 + 8 * ch);
+      const int boff = kmajor_off<TM>(li, c0 + 8 * ch);
 #pragma unroll
       for (int a = 0; a < NDX; ++a) {
         uint4 v;
@@ -488,39 +538,32 @@ __global__ void __launch_bounds__(TTHREADS, 1) tc_sweep_kernel(TcBatch b) {
       if (!ok) { atomicCAS(b.err, 0, HT_ERR_TIMEOUT); *abort_flag = 1; }
       tc_fence_after();
       if (ok) {
-        const uint32_t xa = smem_u32(Xd), ga = smem_u32(Gd);
-        for (int h = 0; h < 2; ++h) {
-          const int gend = h == 0 ? NGROUP : 6;
-          for (int gi = 0; gi < gend; ++gi) {
-            const uint32_t d = tbase + acc_col(h, gi);
-            for (int pi = c_gstart[gi]; pi < c_gstart[gi + 1]; ++pi) {
-              const Pair pr = c_pairs[pi];
-              for (int ks = 0; ks < TW / 16; ++ks)
-                mma_f16(d, sdesc(xa + pr.a * XD_PLANE + ks * 256), sdesc(ga + pr.b * GD_PLANE + 4 * h * 1024 + ks * 256),
-                        (pi > c_gstart[gi] || ks > 0) ? 1u : 0u);
-            }
-          }
-          mma_commit(h == 0 ? bar_m0 : bar_m1);
-        }
+        // A: 128 lines, K chunks 2048 bytes apart; B: 64 output columns, K chunks
+        // 1024 bytes apart, half h = row groups 4h .. 4h + 3
+        const uint64_t da = sdesc(smem_u32(Xd), TM * 16, 128), db = sdesc(smem_u32(Gd), TW * 16, 128);
+        issue_groups<0, 0, NGROUP>(tbase, da, db);
+        mma_commit(bar_m0);
+        issue_groups<1, 0, 6>(tbase, da, db);
+        mma_commit(bar_m1);
         m_pending = true;
       }
     }
     __syncthreads();
     if (*abort_flag) break;
-    // ---- read back: half h, this thread's 16 columns [16 hh, 16 hh + 16) ----
+    // ---- read back: half h, this thread's 8 columns [8 cq, 8 cq + 8) ----
     const int ex = E + F - 2099;  // new x = tot 2^ex
     bool ok = true;
     for (int h = 0; h < 2 && ok; ++h) {
       ok = mbar_wait(h == 0 ? bar_m0 : bar_m1, phase);
       if (!ok) break;
       tc_fence_after();
-      long long tot[16];
+      long long tot[8];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) tot[i] = 0;
-      long long t78[16];
+      for (int i = 0; i < 8; ++i) tot[i] = 0;
+      long long t78[8];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) t78[i] = 0;
-      const uint32_t lanebase = tbase + ((uint32_t)(32 * quarter) << 16) + 16u * hh;
+      for (int i = 0; i < 8; ++i) t78[i] = 0;
+      const uint32_t lanebase = tbase + ((uint32_t)(32 * quarter) << 16) + 8u * cq;
 #pragma unroll 1
       for (int L = 2; L <= 8; ++L) {
         const int ga = (L <= 5) ? L - 2 : 4 + 2 * (L - 6), gb = (L <= 5) ? ga + 1 : ga + 2;
@@ -530,23 +573,27 @@ __global__ void __launch_bounds__(TTHREADS, 1) tc_sweep_kernel(TcBatch b) {
           if (!ok) break;
           tc_fence_after();
         }
-        int s[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) s[i] = 0;
-        for (int gi = ga; gi < gb; ++gi) {
-          uint32_t r[16];
-          tmem_ld16(lanebase + acc_col(h, gi), r);
+        // the level's one or two accumulators, both loads in flight before the wait
+        int s[8];
+        {
+          uint32_t r[8], r2[8];
+          tmem_ld8(lanebase + acc_col(h, ga), r);
+          if (gb - ga > 1) tmem_ld8(lanebase + acc_col(h, ga + 1), r2);
           tmem_wait_ld();
 #pragma unroll
-          for (int i = 0; i < 16; ++i) s[i] += f2i(r[i]);
+          for (int i = 0; i < 8; ++i) s[i] = f2i(r[i]);
+          if (gb - ga > 1) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) s[i] += f2i(r2[i]);
+          }
         }
         if (L <= 6) {
           const int sh = 57 - 9 * L;
 #pragma unroll
-          for (int i = 0; i < 16; ++i) tot[i] += (long long)s[i] << sh;
+          for (int i = 0; i < 8; ++i) tot[i] += (long long)s[i] << sh;
         } else {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) t78[i] = t78[i] * 512 + s[i];
+          for (int i = 0; i < 8; ++i) t78[i] = t78[i] * 512 + s[i];
         }
         if (h == 0 && L == 5) {
           // groups 0-3 of half 0 read: let the MMA thread reuse their columns
@@ -557,16 +604,7 @@ __global__ void __launch_bounds__(TTHREADS, 1) tc_sweep_kernel(TcBatch b) {
             if (!fok) { atomicCAS(b.err, 0, HT_ERR_TIMEOUT); *abort_flag = 1; }
             tc_fence_after();
             if (fok) {
-              const uint32_t xa = smem_u32(Xd), ga2 = smem_u32(Gd);
-              for (int gi = 6; gi < NGROUP; ++gi) {
-                const uint32_t d = tbase + acc_col(1, gi);
-                for (int pi = c_gstart[gi]; pi < c_gstart[gi + 1]; ++pi) {
-                  const Pair pr = c_pairs[pi];
-                  for (int ks = 0; ks < TW / 16; ++ks)
-                    mma_f16(d, sdesc(xa + pr.a * XD_PLANE + ks * 256), sdesc(ga2 + pr.b * GD_PLANE + 4 * 1024 + ks * 256),
-                            (pi > c_gstart[gi] || ks > 0) ? 1u : 0u);
-                }
-              }
+              issue_groups<1, 6, NGROUP>(tbase, sdesc(smem_u32(Xd), TM * 16, 128), sdesc(smem_u32(Gd), TW * 16, 128));
               mma_commit(bar_m2);
             }
           }
@@ -575,9 +613,9 @@ __global__ void __launch_bounds__(TTHREADS, 1) tc_sweep_kernel(TcBatch b) {
       if (!ok) break;
       // levels 7 and 8 rounded once: t78 = S7 2^9 + S8, weight 2^-15
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
+      for (int i = 0; i < 8; ++i) {
         tot[i] += (t78[i] + (1LL << 14)) >> 15;
-        Xf[li * XS + 32 * h + 16 * hh + i] = scaled_double(tot[i], ex);
+        Xf[li * XS + 32 * h + 8 * cq + i] = scaled_double(tot[i], ex);
       }
     }
     if (!ok) { atomicCAS(b.err, 0, HT_ERR_TIMEOUT); *abort_flag = 1; }
