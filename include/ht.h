@@ -171,8 +171,8 @@ int ht_reduce_noalloc(int n, double* A, int lda, double* B, int ldb, double* Q, 
 int ht_philox4x32_10(int count, const uint32_t* in, uint32_t* out, ht_stream_t stream);
 
 /* ht_last_device_status -- status word written by the device during the
- * last call on `stream` from this host thread (HT_OK, HT_ERR_TIMEOUT,
- * HT_ERR_NONFINITE, HT_ERR_INTERNAL). */
+ * last call on `stream` (any host thread; HT_OK, HT_ERR_TIMEOUT,
+ * HT_ERR_NONFINITE, HT_ERR_INTERNAL; HT_OK for a stream without calls). */
 int ht_last_device_status(ht_stream_t stream, int* status);
 
 /* ht_finalize -- release every cached workspace of this process. */

@@ -17,7 +17,15 @@
 
 namespace {
 
-thread_local int t_last_status = HT_OK;
+// device status word of the last call, per stream (ht_last_device_status)
+std::mutex g_status_mu;
+std::vector<std::pair<cudaStream_t, int>> g_status;
+void set_stream_status(cudaStream_t st, int v) {
+  std::lock_guard<std::mutex> lk(g_status_mu);
+  for (auto& e : g_status)
+    if (e.first == st) { e.second = v; return; }
+  g_status.push_back({st, v});
+}
 
 #define HT_CUDA(call)                                  \
   do {                                                 \
@@ -531,7 +539,7 @@ int reduce_impl(int n, double* A, int lda, double* B, int ldb, double* Q, int ld
   if (prec == HT_PREC_EMU && (nb > 32 || (opt && opt->emu_slices != 0 && opt->emu_slices != 6)))
     return HT_ERR_NOT_IMPLEMENTED;
   if (stats) std::memset(stats, 0, sizeof(*stats));
-  t_last_status = HT_OK;
+  set_stream_status(st, HT_OK);
   if (n == 0) return HT_OK;
   if (want_qz) {
     HT_CUDA(ht_launch_set_identity(st, Q, ldq, n));
@@ -675,7 +683,7 @@ int ht_reduce_core(HtWork& w, PanelStatus* host_status, unsigned long long* pt_d
   {
     int derr = 0;
     cudaMemcpy(&derr, w.err, sizeof(int), cudaMemcpyDeviceToHost);
-    t_last_status = derr;
+    set_stream_status(st, derr);
   }
   return result;
 }
@@ -709,9 +717,11 @@ int ht_reduce_batched(int batch, const int* n, double* const* A, const int* lda,
 }
 
 int ht_last_device_status(ht_stream_t stream, int* status) {
-  (void)stream;
   if (!status) return -2;
-  *status = t_last_status;
+  std::lock_guard<std::mutex> lk(g_status_mu);
+  *status = HT_OK;
+  for (const auto& e : g_status)
+    if (e.first == (cudaStream_t)stream) *status = e.second;
   return HT_OK;
 }
 

@@ -20,7 +20,7 @@
 //    product of one digit pair is at most 2^22 and four pairs of one level can
 //    share an FP32 accumulator exactly (level L = a + b of the 1-based digit
 //    indices; levels up to 8 are kept, 27 pairs in 10 accumulators).
-//  * tcgen05.mma (M = 128 lines, N = 32 output columns, K = 16) accumulates
+//  * tcgen05.mma (M = 128 lines, N = 64 output columns, K = 16) accumulates
 //    each group in tensor memory; every thread reads back its line's columns
 //    (tcgen05.ld), converts them to integers, combines the levels in int64 and
 //    writes the new line as FP64, all in integer arithmetic: the sweep issues
@@ -29,11 +29,11 @@
 // The error of a line is that of a rounding at 2^-53 relative to the line's
 // bound: the normwise accuracy of an FP64 product.
 //
-// Launch: one CTA of 256 threads per stripe of 128 lines, sweeping every
+// Launch: one CTA of 512 threads per stripe of 128 lines, sweeping every
 // group of the chain in order; G's digits are staged per group into shared
 // memory with a bulk copy (cp.async.bulk, completion on an mbarrier); the
-// product for output columns 0-31 and 32-63 runs as two sets of MMAs issued by
-// one thread, the second set overlapping the read-back of the first.  Every
+// MMAs are issued by one thread in three commits (levels 2-5, 6-7, 8), the
+// later ones overlapping the read-back of the earlier ones.  Every
 // wait is bounded: on expiry the kernel raises HT_ERR_TIMEOUT, waits (bounded)
 // for what it has in flight, frees its tensor memory and returns.
 #include <cuda_fp16.h>
@@ -217,8 +217,9 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
 }
 
-// kind::f16, D = F32, A = B = F16, both K-major, N = 32, M = 128
-constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(32 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+// kind::f16, D = F32, A = B = F16, both K-major, N = 64, M = 128 (an MMA of
+// this shape costs about what one of N = 32 does: the operand reads dominate)
+constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(64 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 
 __device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
   asm volatile(
@@ -268,10 +269,12 @@ __device__ __forceinline__ void cp_async_wait_all() {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t ta, uint32_t r[8]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(ta));
+__device__ __forceinline__ void tmem_ld16(uint32_t ta, uint32_t r[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(ta));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -376,12 +379,10 @@ __device__ __forceinline__ bool tc_skip(const TcJob& jb, int lb, int lines, int 
   return jb.right ? (lb >= jb.limit_base + lim) : (lb + lines <= jb.limit_base + lim);
 }
 
-// tensor-memory column of accumulator group gi of output half h: half 0 in
-// [0, 320); half 1's groups 0-5 in [320, 512), its groups 6-9 in [0, 128)
-// (reused once half 0's groups 0-3 have been read)
-__device__ __forceinline__ uint32_t acc_col(int h, int gi) {
-  return h == 0 ? 32u * gi : (gi < 6 ? 320u + 32u * gi : 32u * (gi - 6));
-}
+// tensor-memory column of accumulator group gi (64 columns each): groups 0-7
+// fill the 512 columns; groups 8-9 (level 8) reuse those of groups 0-1 once
+// levels 2 and 3 have been read
+__host__ __device__ constexpr uint32_t acc_col(int gi) { return gi < 8 ? 64u * gi : 64u * (gi - 8); }
 
 // The pair table: a, b of pair i, and the first pair of group g (kGs(10) = 27).
 __host__ __device__ constexpr int kPa(int i) {
@@ -397,12 +398,12 @@ __host__ __device__ constexpr int kGs(int i) {
   return t[i];
 }
 
-// MMAs of accumulator groups [G0, G1) of output half H, interleaved across the
-// groups (slot s of every group, then slot s + 1) so that consecutive MMAs go to
+// MMAs of accumulator groups [G0, G1) (N = 64), interleaved across the groups
+// (slot s of every group, then slot s + 1) so that consecutive MMAs go to
 // different accumulators; slot s of a group is its pair s / 4 at k-step s % 4.
 // Fully unrolled: every descriptor is a base descriptor plus a constant (the
 // start-address field takes byte offsets / 16 and does not overflow here).
-template <int H, int G0, int G1>
+template <int G0, int G1>
 __device__ __forceinline__ void issue_groups(uint32_t tbase, uint64_t da, uint64_t db) {
 #pragma unroll
   for (int s = 0; s < 16; ++s) {
@@ -411,9 +412,8 @@ __device__ __forceinline__ void issue_groups(uint32_t tbase, uint64_t da, uint64
       const int pi = kGs(gi) + (s >> 2);
       if (pi < kGs(gi + 1)) {
         const int ks = s & 3;
-        const uint32_t col = H == 0 ? 32u * gi : (gi < 6 ? 320u + 32u * gi : 32u * (gi - 6));
-        mma_f16(tbase + col, da + (uint64_t)((kPa(pi) * XD_PLANE + ks * 2 * (TM * 16)) >> 4),
-                db + (uint64_t)((kPb(pi) * GD_PLANE + 4 * H * 128 + ks * 2 * (TW * 16)) >> 4), s > 0 ? 1u : 0u);
+        mma_f16(tbase + acc_col(gi), da + (uint64_t)((kPa(pi) * XD_PLANE + ks * 2 * (TM * 16)) >> 4),
+                db + (uint64_t)((kPb(pi) * GD_PLANE + ks * 2 * (TW * 16)) >> 4), s > 0 ? 1u : 0u);
       }
     }
   }
@@ -425,10 +425,11 @@ __global__ void __launch_bounds__(TTHREADS, 1) tc_sweep_kernel(TcBatch b) {
   unsigned char* Xd = tsm + OFF_XD;
   unsigned char* Gd = tsm + OFF_GD;
   double* Xf = (double*)(tsm + OFF_XF);
-  uint64_t* bars = (uint64_t*)(tsm + OFF_MISC);  // 0: G copy, 1: MMA half 0, 2: half 1a, 3: half 1b, 4: free
+  uint64_t* bars = (uint64_t*)(tsm + OFF_MISC);  // 0: G copy, 1-3: MMAs of levels 2-5, 6-7, 8, 4: free
   uint32_t* tslot = (uint32_t*)(bars + 8);
   int* Es = (int*)(bars + 16);                   // 4 x TM partial line bounds
   volatile int* abort_flag = (volatile int*)(Es + 4 * TM);
+  volatile int* m2_issued = abort_flag + 1;      // the level-8 MMAs of the current group are in flight
 
   TcJob jb = b.job[0];
 #pragma unroll
@@ -453,6 +454,7 @@ __global__ void __launch_bounds__(TTHREADS, 1) tc_sweep_kernel(TcBatch b) {
     mbar_init(bar_free, TTHREADS);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *abort_flag = 0;
+    *m2_issued = 0;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -531,72 +533,65 @@ __global__ void __launch_bounds__(TTHREADS, 1) tc_sweep_kernel(TcBatch b) {
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    // ---- MMAs: half 0 (all groups), half 1 groups 0-5 ----
+    // ---- MMAs: levels 2-5 (groups 0-3), then levels 6-7 (groups 4-7) ----
+    // A: 128 lines, K chunks 2048 bytes apart; B: 64 output columns, K chunks 1024 apart
+    const uint64_t da = sdesc(smem_u32(Xd), TM * 16, 128), db = sdesc(smem_u32(Gd), TW * 16, 128);
     if (tid == 0) {
       bool ok = mbar_wait(bar_g, phase);
       g_pending = !ok;
       if (!ok) { atomicCAS(b.err, 0, HT_ERR_TIMEOUT); *abort_flag = 1; }
       tc_fence_after();
       if (ok) {
-        // A: 128 lines, K chunks 2048 bytes apart; B: 64 output columns, K chunks
-        // 1024 bytes apart, half h = row groups 4h .. 4h + 3
-        const uint64_t da = sdesc(smem_u32(Xd), TM * 16, 128), db = sdesc(smem_u32(Gd), TW * 16, 128);
-        issue_groups<0, 0, NGROUP>(tbase, da, db);
+        issue_groups<0, 4>(tbase, da, db);
         mma_commit(bar_m0);
-        issue_groups<1, 0, 6>(tbase, da, db);
+        issue_groups<4, 8>(tbase, da, db);
         mma_commit(bar_m1);
         m_pending = true;
       }
     }
     __syncthreads();
     if (*abort_flag) break;
-    // ---- read back: half h, this thread's 8 columns [8 cq, 8 cq + 8) ----
+    // ---- read back: this thread's 16 output columns [16 cq, 16 cq + 16) ----
     const int ex = E + F - 2099;  // new x = tot 2^ex
-    bool ok = true;
-    for (int h = 0; h < 2 && ok; ++h) {
-      ok = mbar_wait(h == 0 ? bar_m0 : bar_m1, phase);
-      if (!ok) break;
+    bool ok = mbar_wait(bar_m0, phase);
+    if (ok) {
       tc_fence_after();
-      long long tot[8];
+      long long tot[16], t78[16];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) tot[i] = 0;
-      long long t78[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) t78[i] = 0;
-      const uint32_t lanebase = tbase + ((uint32_t)(32 * quarter) << 16) + 8u * cq;
+      for (int i = 0; i < 16; ++i) { tot[i] = 0; t78[i] = 0; }
+      const uint32_t lanebase = tbase + ((uint32_t)(32 * quarter) << 16) + 16u * cq;
 #pragma unroll 1
-      for (int L = 2; L <= 8; ++L) {
+      for (int L = 2; L <= 8 && ok; ++L) {
         const int ga = (L <= 5) ? L - 2 : 4 + 2 * (L - 6), gb = (L <= 5) ? ga + 1 : ga + 2;
-        if (h == 1 && L == 7) {
-          // half 1's groups 6-9 live where half 0's groups 0-3 were
-          ok = mbar_wait(bar_m2, phase);
+        if (L == 6 || L == 8) {
+          ok = mbar_wait(L == 6 ? bar_m1 : bar_m2, phase);
           if (!ok) break;
           tc_fence_after();
         }
         // the level's one or two accumulators, both loads in flight before the wait
-        int s[8];
+        int sl[16];
         {
-          uint32_t r[8], r2[8];
-          tmem_ld8(lanebase + acc_col(h, ga), r);
-          if (gb - ga > 1) tmem_ld8(lanebase + acc_col(h, ga + 1), r2);
+          uint32_t r[16], r2[16];
+          tmem_ld16(lanebase + acc_col(ga), r);
+          if (gb - ga > 1) tmem_ld16(lanebase + acc_col(ga + 1), r2);
           tmem_wait_ld();
 #pragma unroll
-          for (int i = 0; i < 8; ++i) s[i] = f2i(r[i]);
+          for (int i = 0; i < 16; ++i) sl[i] = f2i(r[i]);
           if (gb - ga > 1) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) s[i] += f2i(r2[i]);
+            for (int i = 0; i < 16; ++i) sl[i] += f2i(r2[i]);
           }
         }
         if (L <= 6) {
           const int sh = 57 - 9 * L;
 #pragma unroll
-          for (int i = 0; i < 8; ++i) tot[i] += (long long)s[i] << sh;
+          for (int i = 0; i < 16; ++i) tot[i] += (long long)sl[i] << sh;
         } else {
 #pragma unroll
-          for (int i = 0; i < 8; ++i) t78[i] = t78[i] * 512 + s[i];
+          for (int i = 0; i < 16; ++i) t78[i] = t78[i] * 512 + sl[i];
         }
-        if (h == 0 && L == 5) {
-          // groups 0-3 of half 0 read: let the MMA thread reuse their columns
+        if (L == 3) {
+          // levels 2-3 (groups 0-1) read: level 8 (groups 8-9) may take their columns
           tc_fence_before();
           mbar_arrive(bar_free);
           if (tid == 0) {
@@ -604,18 +599,20 @@ __global__ void __launch_bounds__(TTHREADS, 1) tc_sweep_kernel(TcBatch b) {
             if (!fok) { atomicCAS(b.err, 0, HT_ERR_TIMEOUT); *abort_flag = 1; }
             tc_fence_after();
             if (fok) {
-              issue_groups<1, 6, NGROUP>(tbase, sdesc(smem_u32(Xd), TM * 16, 128), sdesc(smem_u32(Gd), TW * 16, 128));
+              issue_groups<8, NGROUP>(tbase, da, db);
               mma_commit(bar_m2);
+              *m2_issued = 1;
             }
           }
         }
       }
-      if (!ok) break;
-      // levels 7 and 8 rounded once: t78 = S7 2^9 + S8, weight 2^-15
+      if (ok) {
+        // levels 7 and 8 rounded once: t78 = S7 2^9 + S8, weight 2^-15
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        tot[i] += (t78[i] + (1LL << 14)) >> 15;
-        Xf[li * XS + 32 * h + 8 * cq + i] = scaled_double(tot[i], ex);
+        for (int i = 0; i < 16; ++i) {
+          tot[i] += (t78[i] + (1LL << 14)) >> 15;
+          Xf[li * XS + 16 * cq + i] = scaled_double(tot[i], ex);
+        }
       }
     }
     if (!ok) { atomicCAS(b.err, 0, HT_ERR_TIMEOUT); *abort_flag = 1; }
@@ -624,6 +621,7 @@ __global__ void __launch_bounds__(TTHREADS, 1) tc_sweep_kernel(TcBatch b) {
     if (*abort_flag) break;
     m_pending = false;
     g_pending = false;
+    if (tid == 0) *m2_issued = 0;
     // ---- prefetch the next group's digits (all MMAs of this one are done) ----
     const int tn = next_group(t + 1);
     if (tid == 0 && tn < b.ngroups) {
@@ -654,6 +652,7 @@ __global__ void __launch_bounds__(TTHREADS, 1) tc_sweep_kernel(TcBatch b) {
       mbar_wait(bar_m0, phase);
       mbar_wait(bar_m1, phase);
     }
+    if (*m2_issued) mbar_wait(bar_m2, phase);
   }
   tc_fence_before();
   __syncthreads();

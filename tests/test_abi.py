@@ -70,3 +70,13 @@ def test_options_rejected_before_device_work(htlib):
     import ctypes
     rc = L.ht_reduce_ex(4, 0x1000, 4, 0x1000, 4, 0x1000, 4, 0x1000, 4, 1, ctypes.byref(opts), None, None)
     assert rc == htlib.HT_ERR_NOT_IMPLEMENTED
+
+
+def test_last_device_status_is_per_stream(htlib):
+    """ht_last_device_status reads the status of the last call on the given
+    stream; a stream without calls reports HT_OK (no CUDA call is made)."""
+    import ctypes
+    st = ctypes.c_int(-7)
+    assert htlib.lib().ht_last_device_status(ctypes.c_void_p(0x7777), ctypes.byref(st)) == htlib.HT_OK
+    assert st.value == htlib.HT_OK
+    assert htlib.lib().ht_last_device_status(None, None) == -2
