@@ -322,7 +322,7 @@ cudaError_t run_sweep(Ctx& c, const HtSweepJob* jobs, int njobs, const double* w
 // the lines its own steps need, followed by an emulated sweep of the
 // segment's transforms on the remaining lines of B (rows 0 .. j as well for
 // the RQ chain); otherwise one launch.
-constexpr int RS_SEG = 32;
+constexpr int RS_SEG = 64;
 // flops of restore steps [ta, tb) whose updates reach the lines [blo, bhi): the
 // factorization of each block and its transform on the trailing lines of B
 double fl_restore(int mode, int p, int k, int ta, int tb, int blo, int bhi) {
