@@ -104,6 +104,8 @@ size_t ht_layout_work(HtWork& w, char* b, int n, int nb, int G, unsigned long lo
   const size_t oCf = take((size_t)n + 8);  // 2 (n + 8) ints
   const size_t oRc = take(2);
   const size_t oRt = take(nn + 2 * HT_NB_MAX);
+  // work-unit counters of the tcgen05 sweeps: 1 + line blocks of up to HT_SWEEP_MAXJOBS jobs
+  const size_t oTs = take((size_t)(1 + HT_SWEEP_MAXJOBS * (n / 128 + 1)) / 2 + 1);
   if (!b) return total;
   w.U = (double*)(b + oU); w.V = (double*)(b + oV); w.Y = (double*)(b + oY);
   w.S = (double*)(b + oS); w.T = (double*)(b + oT);
@@ -140,6 +142,7 @@ size_t ht_layout_work(HtWork& w, char* b, int n, int nb, int G, unsigned long lo
   w.rcount = (int*)(b + oRc);
   w.cflags = (int*)(b + oCf);
   w.rtaus = (double*)(b + oRt);
+  w.tc_sched = (int*)(b + oTs);
   w.wpart = (double*)(b + oWpart);
   w.tstore = (double*)(b + oTst);
   if (pt) *pt = (unsigned long long*)(b + oPt);
@@ -308,7 +311,7 @@ cudaError_t run_sweep(Ctx& c, const HtSweepJob* jobs, int njobs, const double* w
                       int t0, int t1) {
   if (c.w->prec == HT_PREC_EMU && c.w->tc)
     return ht_tc_sweep_multi(c.st, jobs, njobs, wy, wst, mode, p, k, t0, t1, c.w->emu_dig, c.w->emu_exps,
-                             c.w->emu_geo, c.w->emu_cap, c.w->err);
+                             c.w->emu_geo, c.w->emu_cap, c.w->tc_sched, c.w->err);
   if (c.w->prec == HT_PREC_EMU)
     return ht_emu_sweep_multi(c.st, jobs, njobs, wy, wst, mode, p, k, t0, t1, c.w->emu_dig, c.w->emu_exps,
                               c.w->emu_cap, c.w->emu_mwy, c.w->emu_geo);

@@ -143,6 +143,7 @@ struct HtWork {
   long spin;               // polls before a bounded device wait gives up (HT_SPIN_LIMIT by default)
   int tc;                  // emulated sweeps on tcgen05 (ht_tc.cu) instead of mma.sync (ht_emu.cu)
   int* cflags;             // wavefront chains: columns published per window (2 (n + 8) ints)
+  int* tc_sched;           // work-unit counters of the tcgen05 sweeps (1 + 3 (n / 128 + 1) ints)
   cudaStream_t stream;
 };
 #define HT_PART_STRIDE 80   // >= nb + 8 for nb <= 64 ... plus norms
@@ -207,11 +208,12 @@ cudaError_t ht_emu_sweep_multi(cudaStream_t st, const HtSweepJob* jobs, int njob
 size_t ht_emu_window_bytes(int nb);
 // as ht_sweep_multi with FP64 emulated on the tcgen05 tensor cores (ht_tc.cu):
 // consecutive windows grouped into products of at most 64 x 64, `cap` groups per
-// launch, dig: cap * ht_tc_group_bytes() bytes, exps: cap ints, geo: cap int4;
+// launch, dig: cap * ht_tc_group_bytes() bytes, exps: cap ints, geo: cap int4,
+// sched: 1 + (line blocks of 128 lines of all jobs) ints of scratch;
 // k <= 32; a bounded wait that gives up raises HT_ERR_TIMEOUT in *err
 cudaError_t ht_tc_sweep_multi(cudaStream_t st, const HtSweepJob* jobs, int njobs, const double* wy, long stride,
                               int mode, int p, int k, int t0, int t1, void* dig, int* exps, void* geo, int cap,
-                              int* err);
+                              int* sched, int* err);
 int ht_tc_group(int k);
 size_t ht_tc_group_bytes();
 size_t ht_emu_merge_doubles(int cap);

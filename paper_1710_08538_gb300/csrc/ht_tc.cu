@@ -29,13 +29,16 @@
 // The error of a line is that of a rounding at 2^-53 relative to the line's
 // bound: the normwise accuracy of an FP64 product.
 //
-// Launch: one CTA of 512 threads per stripe of 128 lines, sweeping every
-// group of the chain in order; G's digits are staged per group into shared
-// memory with a bulk copy (cp.async.bulk, completion on an mbarrier); the
-// MMAs are issued by one thread in three commits (levels 2-5, 6-7, 8), the
-// later ones overlapping the read-back of the earlier ones.  Every
-// wait is bounded: on expiry the kernel raises HT_ERR_TIMEOUT, waits (bounded)
-// for what it has in flight, frees its tensor memory and returns.
+// Launch: a persistent grid of CTAs of 512 threads (one per SM) takes work
+// units from a counter: a unit is one stripe of 128 lines and a chunk of
+// consecutive groups, units of one stripe in chunk order (a unit waits for
+// the stripe's previous chunk), so that the grid does not round up to whole
+// waves of stripes.  G's digits are staged per group into shared memory with
+// a bulk copy (cp.async.bulk, completion on an mbarrier); the MMAs are issued
+// by one thread in three commits (levels 2-5, 6-7, 8), the later ones
+// overlapping the read-back of the earlier ones.  Every wait is bounded: on
+// expiry the kernel raises HT_ERR_TIMEOUT, waits (bounded) for what it has in
+// flight, frees its tensor memory and returns.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -266,6 +269,17 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
 }
+// bounded wait until *f >= v (acquire); gives up when the error word is set
+__device__ bool flag_wait(const int* f, int v, const int* err) {
+  for (long it = 0; it < TC_POLLS; ++it) {
+    int x;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(x) : "l"(f) : "memory");
+    if (x >= v) return true;
+    if (*(const volatile int*)err != 0) return false;
+    __nanosleep(64);
+  }
+  return false;
+}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -372,6 +386,9 @@ struct TcBatch {
   const int* exps;
   const int4* geo;
   int* err;
+  // work units: (chunk c of wpc consecutive groups, line block gl), unit c nlb + gl
+  int nlb, wpc, nunits;
+  int* sched;            // [0] next unit, [1 + gl] chunks of line block gl done (zeroed per launch)
 };
 
 __device__ __forceinline__ bool tc_skip(const TcJob& jb, int lb, int lines, int lim) {
@@ -430,19 +447,11 @@ __global__ void __launch_bounds__(TTHREADS, 1) tc_sweep_kernel(TcBatch b) {
   int* Es = (int*)(bars + 16);                   // 4 x TM partial line bounds
   volatile int* abort_flag = (volatile int*)(Es + 4 * TM);
   volatile int* m2_issued = abort_flag + 1;      // the level-8 MMAs of the current group are in flight
+  volatile int* unit_sl = abort_flag + 2;        // the unit this CTA works on
 
-  TcJob jb = b.job[0];
-#pragma unroll
-  for (int i = 1; i < HT_SWEEP_MAXJOBS; ++i)
-    if (i < b.njobs && (int)blockIdx.x >= b.job[i].cta0) jb = b.job[i];
-  const int lb = jb.line0 + ((int)blockIdx.x - jb.cta0) * TM;
-  const int lines = min(TM, jb.line0 + jb.nlines - lb);
-  if (lines <= 0) return;  // uniform over the CTA, before any barrier or allocation
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int quarter = warp & 3, cq = warp >> 2;
   const int li = 32 * quarter + lane;  // this thread's line (tensor-memory lane); cq: its column quarter
-  double* X = jb.X;
-  const long ldx = jb.ldx;
   const uint32_t bar_g = smem_u32(bars + 0), bar_m0 = smem_u32(bars + 1), bar_m1 = smem_u32(bars + 2),
                  bar_m2 = smem_u32(bars + 3), bar_free = smem_u32(bars + 4);
 
@@ -466,24 +475,46 @@ __global__ void __launch_bounds__(TTHREADS, 1) tc_sweep_kernel(TcBatch b) {
   tc_fence_after();
   const uint32_t tbase = *tslot;
 
-  // the first group this stripe takes
+  uint32_t phase = 0;
+  bool g_pending = false;  // a bulk copy of G digits is in flight
+  bool m_pending = false;  // MMAs in flight (for the clean-up after a timeout)
+  for (;;) {
+  // ---- the next unit: line block gl, groups [tlo, thi) ----
+  if (tid == 0) *unit_sl = atomicAdd(b.sched, 1);
+  __syncthreads();
+  const int u = *unit_sl;
+  if (u >= b.nunits) break;
+  const int cu = u / b.nlb, gl = u - cu * b.nlb;
+  TcJob jb = b.job[0];
+#pragma unroll
+  for (int i = 1; i < HT_SWEEP_MAXJOBS; ++i)
+    if (i < b.njobs && gl >= b.job[i].cta0) jb = b.job[i];
+  const int lb = jb.line0 + (gl - jb.cta0) * TM;
+  const int lines = min(TM, jb.line0 + jb.nlines - lb);  // >= 1: line blocks cover the jobs' lines
+  double* X = jb.X;
+  const long ldx = jb.ldx;
+  const int tlo = cu * b.wpc, thi = min(b.ngroups, tlo + b.wpc);
+  if (cu > 0 && tid == 0) {
+    // the stripe's previous chunk (taken earlier by a resident CTA) must be written
+    if (!flag_wait(b.sched + 1 + gl, cu, b.err)) { atomicCAS(b.err, 0, HT_ERR_TIMEOUT); *abort_flag = 1; }
+  }
+  __syncthreads();
+  if (*abort_flag) break;
+  // the first group this unit takes
   auto next_group = [&](int from) {
-    for (int t = from; t < b.ngroups; ++t) {
+    for (int t = from; t < thi; ++t) {
       const int4 gq = b.geo[t];
       if (!tc_skip(jb, lb, lines, gq.z)) return t;
     }
-    return b.ngroups;
+    return thi;
   };
-  int t = next_group(0);
-  bool g_pending = false;  // a bulk copy of G digits is in flight
-  if (tid == 0 && t < b.ngroups) {
+  int t = next_group(tlo);
+  if (tid == 0 && t < thi) {
     mbar_expect_tx(bar_g, GD_BYTES);
     bulk_g2s(smem_u32(Gd), b.dig + (size_t)t * (GD_BYTES / 2), GD_BYTES, bar_g);
   }
-  g_pending = t < b.ngroups;
-  uint32_t phase = 0;
-  bool m_pending = false;  // MMAs in flight (for the clean-up after a timeout)
-  while (t < b.ngroups) {
+  g_pending = t < thi;
+  while (t < thi) {
     const int4 gq = b.geo[t];
     const int off = gq.x, w = gq.y;
     const int o0 = jb.origin + off;
@@ -624,11 +655,11 @@ __global__ void __launch_bounds__(TTHREADS, 1) tc_sweep_kernel(TcBatch b) {
     if (tid == 0) *m2_issued = 0;
     // ---- prefetch the next group's digits (all MMAs of this one are done) ----
     const int tn = next_group(t + 1);
-    if (tid == 0 && tn < b.ngroups) {
+    if (tid == 0 && tn < thi) {
       mbar_expect_tx(bar_g, GD_BYTES);
       bulk_g2s(smem_u32(Gd), b.dig + (size_t)tn * (GD_BYTES / 2), GD_BYTES, bar_g);
     }
-    g_pending = tn < b.ngroups;
+    g_pending = tn < thi;
     // ---- Xf -> stripe ----
     if (jb.right) {
       for (int e = tid; e < TM * TW; e += TTHREADS) {
@@ -644,6 +675,13 @@ __global__ void __launch_bounds__(TTHREADS, 1) tc_sweep_kernel(TcBatch b) {
     __syncthreads();
     phase ^= 1u;
     t = tn;
+  }
+  if (*abort_flag) break;
+  // ---- the unit's lines are written: release its chunk to the next one ----
+  if (tid == 0) {
+    __threadfence();
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(b.sched + 1 + gl), "r"(cu + 1) : "memory");
+  }
   }
   // ---- clean-up: after a timeout, wait (bounded) for what is in flight ----
   if (*abort_flag && tid == 0) {
@@ -674,7 +712,38 @@ cudaError_t tc_attr() {
   return e;
 }
 
+int tc_sm_count() {
+  static int sms[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return 0;
+  if (sms[dev] == 0 && cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    sms[dev] = 0;
+    return 0;
+  }
+  return sms[dev];
+}
+
 }  // namespace
+
+// Groups per work unit for nlb stripes of ng groups on `sms` resident CTAs:
+// a stripe's units run one after another, so the sweep takes at least ng
+// group times, and ceil(nlb nc / sms) rounds of ng / nc group times with nc
+// chunks; the fewest chunks (of at least 4 groups) that come within 2% of the
+// best bound.
+static int tc_chunk(int nlb, int ng, int sms) {
+  auto cost = [&](int nc) {
+    const int wpc = (ng + nc - 1) / nc;
+    const int ncr = (ng + wpc - 1) / wpc;
+    const double rounds = (double)(((long)nlb * ncr + sms - 1) / sms);
+    return std::max((double)ng, rounds * wpc);
+  };
+  const int ncmax = std::max(1, std::min(64, ng / 4));
+  double best = cost(1);
+  for (int nc = 2; nc <= ncmax; ++nc) best = std::min(best, cost(nc));
+  for (int nc = 1; nc <= ncmax; ++nc)
+    if (cost(nc) <= 1.02 * best) return (ng + nc - 1) / nc;
+  return ng;
+}
 
 // windows per group: the union of g consecutive windows of a chain with k
 // reflectors spans at most (g + 1) k <= 64 rows
@@ -683,7 +752,7 @@ size_t ht_tc_group_bytes() { return GD_BYTES; }
 
 cudaError_t ht_tc_sweep_multi(cudaStream_t st, const HtSweepJob* jobs, int njobs, const double* wy, long stride,
                               int mode, int p, int k, int t0, int t1, void* dig, int* exps, void* geo, int cap,
-                              int* err) {
+                              int* sched, int* err) {
   if (njobs < 1 || njobs > HT_SWEEP_MAXJOBS) return cudaErrorInvalidValue;
   if (t1 <= t0) return cudaSuccess;
   if (k < 1 || 2 * k > TW) return cudaErrorNotSupported;
@@ -705,6 +774,10 @@ cudaError_t ht_tc_sweep_multi(cudaStream_t st, const HtSweepJob* jobs, int njobs
   bt.exps = exps;
   bt.geo = (const int4*)geo;
   bt.err = err;
+  bt.nlb = ctas;
+  bt.sched = sched;
+  const int sms = tc_sm_count();
+  if (sms <= 0) return cudaErrorUnknown;
   const int g = ht_tc_group(k);
   const int ng = (t1 - t0 + g - 1) / g;
   for (int m0 = 0; m0 < ng; m0 += cap) {
@@ -712,7 +785,11 @@ cudaError_t ht_tc_sweep_multi(cudaStream_t st, const HtSweepJob* jobs, int njobs
     const int ta = t0 + m0 * g, tb = std::min(t1, ta + mc * g);
     tc_prep_kernel<<<mc, TTHREADS, PREP_SMEM, st>>>(wy, stride, mode, p, k, g, ta, tb, (uint16_t*)dig, exps, (int4*)geo);
     bt.ngroups = mc;
-    tc_sweep_kernel<<<ctas, TTHREADS, SMEM_BYTES, st>>>(bt);
+    bt.wpc = tc_chunk(ctas, mc, sms);
+    bt.nunits = ctas * ((mc + bt.wpc - 1) / bt.wpc);
+    e = cudaMemsetAsync(sched, 0, (size_t)(1 + ctas) * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    tc_sweep_kernel<<<std::min(bt.nunits, sms), TTHREADS, SMEM_BYTES, st>>>(bt);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
