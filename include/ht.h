@@ -81,6 +81,8 @@ enum {
   HT_CLASS_RANKK = 4,        /* rank-k corrections with V1, L1, U1, R1 */
   HT_CLASS_GEMM = 5,         /* deferred Y rows (Remark 3.1), spike update */
   HT_CLASS_OTHER = 6,        /* preparation of B, zeroing, copies */
+  HT_CLASS_SIDE = 7,         /* Q and Z updates on the library's second stream, overlapping
+                                the others (emulated path; its time is not additive) */
   HT_NCLASS = 8
 };
 

@@ -56,7 +56,7 @@ class HtStats(ctypes.Structure):
         return out
 
 
-CLASS_NAMES = ["panel", "chain_factor", "restore", "sweep", "rankk", "gemm", "other", "unused"]
+CLASS_NAMES = ["panel", "chain_factor", "restore", "sweep", "rankk", "gemm", "other", "side"]
 
 
 class HtError(RuntimeError):

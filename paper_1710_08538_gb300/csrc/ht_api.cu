@@ -57,7 +57,7 @@ size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 // Workspace layout for order n, panel width nb and G CTAs in the cooperative
 // panel: returns the bytes needed; when b is not null, carves the pointers of
 // w (and *pt, the profile timers) out of the buffer at b.
-size_t ht_layout_work(HtWork& w, char* b, int n, int nb, int G, unsigned long long** pt) {
+size_t ht_layout_work(HtWork& w, char* b, int n, int nb, int G, unsigned long long** pt, bool side) {
   std::memset(&w, 0, sizeof(w));
   w.n = n;
   w.nb = nb;
@@ -106,6 +106,11 @@ size_t ht_layout_work(HtWork& w, char* b, int n, int nb, int G, unsigned long lo
   const size_t oRt = take(nn + 2 * HT_NB_MAX);
   // work-unit counters of the tcgen05 sweeps: 1 + line blocks of up to HT_SWEEP_MAXJOBS jobs
   const size_t oTs = take((size_t)(1 + HT_SWEEP_MAXJOBS * (n / 128 + 1)) / 2 + 1);
+  // the side stream's sweeps: digits, bounds, table, unit counters of their own
+  const size_t oEmu2 = side ? take(emu_win ? (emu_win * w.emu_cap + sizeof(double) - 1) / sizeof(double) : 0) : 0;
+  const size_t oEmuE2 = side ? take((size_t)w.emu_cap) : 0;
+  const size_t oEmuG2 = side ? take(2 * (size_t)w.emu_cap) : 0;
+  const size_t oTs2 = side ? take((size_t)(1 + HT_SWEEP_MAXJOBS * (n / 128 + 1)) / 2 + 1) : 0;
   if (!b) return total;
   w.U = (double*)(b + oU); w.V = (double*)(b + oV); w.Y = (double*)(b + oY);
   w.S = (double*)(b + oS); w.T = (double*)(b + oT);
@@ -143,6 +148,12 @@ size_t ht_layout_work(HtWork& w, char* b, int n, int nb, int G, unsigned long lo
   w.cflags = (int*)(b + oCf);
   w.rtaus = (double*)(b + oRt);
   w.tc_sched = (int*)(b + oTs);
+  if (side) {
+    w.emu_dig2 = emu_win ? (void*)(b + oEmu2) : nullptr;
+    w.emu_exps2 = (int*)(b + oEmuE2);
+    w.emu_geo2 = (void*)(b + oEmuG2);
+    w.tc_sched2 = (int*)(b + oTs2);
+  }
   w.wpart = (double*)(b + oWpart);
   w.tstore = (double*)(b + oTst);
   if (pt) *pt = (unsigned long long*)(b + oPt);
@@ -154,12 +165,24 @@ namespace {
 int alloc_work(PoolEntry* e, int n, int nb) {
   HtWork& w = e->w;
   const int G = ht_panel_max_ctas(nb);
-  const size_t total = ht_layout_work(w, nullptr, n, nb, G, nullptr);
+  const size_t total = ht_layout_work(w, nullptr, n, nb, G, nullptr, true);
   void* base = nullptr;
   if (cudaMalloc(&base, total) != cudaSuccess) return HT_ERR_NOMEM;
   cudaMemset(base, 0, total);
-  ht_layout_work(w, (char*)base, n, nb, G, &e->pt_dev);
+  ht_layout_work(w, (char*)base, n, nb, G, &e->pt_dev, true);
   e->base = base;
+  // the side stream of the Q / Z updates and its events (without them, one stream)
+  if (cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking) != cudaSuccess) {
+    w.side = nullptr;
+    cudaGetLastError();
+  }
+  for (int i = 0; i < 5 && w.side; ++i)
+    if (cudaEventCreateWithFlags(&w.side_ev[i], cudaEventDisableTiming) != cudaSuccess) {
+      for (int q = 0; q < i; ++q) cudaEventDestroy(w.side_ev[q]);
+      cudaStreamDestroy(w.side);
+      w.side = nullptr;
+      cudaGetLastError();
+    }
   if (cudaMallocHost((void**)&e->host_status, sizeof(PanelStatus)) != cudaSuccess) {
     cudaFree(base);
     return HT_ERR_NOMEM;
@@ -208,23 +231,27 @@ struct Prof {
   }
   int cls = 0;
   cudaEvent_t cur = nullptr;
-  void begin(int c) {
+  cudaStream_t side = nullptr;  // the side stream (also synchronised by resolve)
+  cudaStream_t lst = nullptr;   // stream of the current launch
+  void begin(int c, cudaStream_t s = nullptr) {
     cls = c;
+    lst = s ? s : st;
     if (!on) return;
     cur = get();
-    cudaEventRecord(cur, st);
+    cudaEventRecord(cur, lst);
   }
   void end(double fl) {
     flops[cls] += fl;
     launches[cls] += 1;
     if (!on) return;
     cudaEvent_t e = get();
-    cudaEventRecord(e, st);
+    cudaEventRecord(e, lst);
     pending.push_back({cls, {cur, e}});
   }
   void resolve() {
     if (!on) return;
     cudaStreamSynchronize(st);
+    if (side) cudaStreamSynchronize(side);
     for (auto& p : pending) {
       float t = 0.f;
       cudaEventElapsedTime(&t, p.second.first, p.second.second);
@@ -249,6 +276,8 @@ struct Ctx {
   int want_qz;
   double flops;
   Prof* prof;
+  // a mode-3 Q sweep left to the side stream of the next absorption (or the end)
+  struct { bool on; int p, k, j, nlb; long wst; } pendq;
 };
 
 // Launch `expr` as one timed launch of class `cls` with `fl` algorithmic flops.
@@ -259,6 +288,16 @@ struct Ctx {
     if (e_ != cudaSuccess) return e_;    \
     c.prof->end(fl);                     \
     c.flops += (fl);                     \
+  } while (0)
+
+// the same on the side stream (class HT_CLASS_SIDE)
+#define LAUNCH_SIDE(fl, expr)                     \
+  do {                                            \
+    c.prof->begin(HT_CLASS_SIDE, c.w->side);      \
+    cudaError_t e_ = (expr);                      \
+    if (e_ != cudaSuccess) return e_;             \
+    c.prof->end(fl);                              \
+    c.flops += (fl);                              \
   } while (0)
 
 #define CK(call)                         \
@@ -306,9 +345,28 @@ double fl_sweep(int mode, int p, int k, int nwin, double lines, int limit_base, 
   return f;
 }
 
+// Overlap of the Q / Z updates (emulated path): the main stream's cooperative
+// restore launches take at most RS_MAIN_CTAS CTAs, the side stream's sweeps the
+// other SMs, so that both are resident together whatever runs first.
+constexpr int RS_MAIN_CTAS = 88;
+int sm_count() {
+  static int sms[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (sms[dev] == 0) cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+  return sms[dev];
+}
+int side_ctas() { return std::max(1, sm_count() - RS_MAIN_CTAS); }
+
 // One fused chain application, native FP64 or emulated (HT_PREC_EMU).
 cudaError_t run_sweep(Ctx& c, const HtSweepJob* jobs, int njobs, const double* wy, long wst, int mode, int p, int k,
-                      int t0, int t1) {
+                      int t0, int t1, bool on_side = false) {
+  if (on_side) {
+    // the side stream: its own buffers, at most RS_SIDE_CTAS CTAs (the rest of the
+    // GPU stays free for the cooperative restore of the main stream)
+    return ht_tc_sweep_multi(c.w->side, jobs, njobs, wy, wst, mode, p, k, t0, t1, c.w->emu_dig2, c.w->emu_exps2,
+                             c.w->emu_geo2, c.w->emu_cap, c.w->tc_sched2, c.w->err, side_ctas());
+  }
   if (c.w->prec == HT_PREC_EMU && c.w->tc)
     return ht_tc_sweep_multi(c.st, jobs, njobs, wy, wst, mode, p, k, t0, t1, c.w->emu_dig, c.w->emu_exps,
                              c.w->emu_geo, c.w->emu_cap, c.w->tc_sched, c.w->err);
@@ -351,7 +409,7 @@ double fl_restore(int mode, int p, int k, int ta, int tb, int blo, int bhi) {
   return f;
 }
 
-cudaError_t restore_chain(Ctx& c, int mode, int p, int k, int j, double* wy, long wst, bool seg) {
+cudaError_t restore_chain(Ctx& c, int mode, int p, int k, int j, double* wy, long wst, bool seg, int max_ctas = 0) {
   HtWork& w = *c.w;
   const int nsteps = ht_restore_steps(mode, p, k);
   if (nsteps <= 0) return cudaSuccess;
@@ -368,7 +426,7 @@ cudaError_t restore_chain(Ctx& c, int mode, int p, int k, int j, double* wy, lon
     if (tb < nsteps) ht_restore_band(mode, p, k, tb, &blo0, &bhi0);
     LAUNCH(HT_CLASS_RESTORE, fl_restore(mode, p, k, ta, tb, blo0, bhi0),
            ht_launch_restore(c.st, mode, p, k, j, c.n, c.B, c.ldb, wy, wst, w.tstore, w.rtaus, w.rcount, w.err,
-                             w.ptime, w.spin, ta, tb));
+                             w.ptime, w.spin, ta, tb, max_ctas));
     int blo = 0, bhi = p;
     if (tb < nsteps) ht_restore_band(mode, p, k, tb, &blo, &bhi);
     if (mode == 2) {
@@ -385,6 +443,21 @@ cudaError_t restore_chain(Ctx& c, int mode, int p, int k, int j, double* wy, lon
     }
   }
   return cudaSuccess;
+}
+
+// The deferred last Q sweep (mode 3, Sec. 3.3.2 (d) step 4) of the previous
+// absorption, on the side stream; side_ev[3] marks its end (the main stream
+// waits for it before the QR restore overwrites its WY store).
+cudaError_t flush_pendq(Ctx& c) {
+  HtWork& w = *c.w;
+  if (c.pendq.on) {
+    const auto& d = c.pendq;
+    const HtSweepJob jq = {c.Q, c.ldq, 1, 0, c.n, d.j + 1, 0, 0};
+    LAUNCH_SIDE(fl_sweep(3, d.p, d.k, d.nlb, c.n, -1, false),
+                run_sweep(c, &jq, 1, w.wyLR, d.wst, 3, d.p, d.k, 0, d.nlb, true));
+    c.pendq.on = false;
+  }
+  return cudaEventRecord(w.side_ev[3], w.side);
 }
 
 // Absorption of k right and k left reflectors (Sec. 3.3.1 and 3.3.2).
@@ -425,36 +498,59 @@ cudaError_t absorb(Ctx& c, int s, int k) {
   else
     LAUNCH(HT_CLASS_CHAIN_FACTOR, 2.0 * fl_chain(p, k),
            ht_launch_chains(st, V + k, w.U2w, n, p, k, w.wyR, w.wyL, wst, w.L1, w.R1));
+  // Emulated path with a side stream: the Q and Z updates (sweeps and rank-k
+  // corrections) go to the side stream, launched when the main stream starts a
+  // restore chain, which leaves most of the GPU idle (the restore takes at most
+  // RS_MAIN_CTAS CTAs): during the RQ restore the previous absorption's last Q
+  // sweep (mode 3) and the Z sweep and rank-k of this one; during the QR restore
+  // the Q sweep (mode 1), the second Z sweep (mode 2) and the Q rank-k.  The
+  // main stream waits for the side stream before the next panel (the data these
+  // read) and for the deferred Q sweep before the QR restore (its WY store).
+  const int nbr = ht_num_right_blocks(p, k);
+  const int nlb = ht_num_left_blocks(p, k);
+  const bool seg = w.prec == HT_PREC_EMU && k <= 32;
+  const bool ov = seg && w.side && w.tc;
+  const int rs_ctas = ov ? RS_MAIN_CTAS : 0;
+  const double fl_rk = dn * (4.0 * k * k + 6.0 * k * k);
+  const double fl_rkl = 8.0 * k * k + 2.0 * k * k;
   // (c)-(e) step 1: A, Z, B columns j+1..n-1 times the chain, one fused launch
   {
     const HtSweepJob jobs[3] = {{A, lda, 1, 0, n, j + 1, 0, 0},
                                 {B, ldb, 1, 0, n, j + 1, 1, j + 1},
-                                {Z, ldz, 1, 0, c.want_qz ? n : 0, j + 1, 0, 0}};
+                                {Z, ldz, 1, 0, (c.want_qz && !ov) ? n : 0, j + 1, 0, 0}};
     const double fl = fl_sweep(0, p, k, nwr, n, j + 1, false) +
-                      (c.want_qz ? 2.0 : 1.0) * fl_sweep(0, p, k, nwr, n, -1, false);
+                      ((c.want_qz && !ov) ? 2.0 : 1.0) * fl_sweep(0, p, k, nwr, n, -1, false);
     LAUNCH(HT_CLASS_SWEEP, fl, run_sweep(c, jobs, 3, w.wyR, wst, 0, p, k, 0, nwr));
   }
   // (c)/(d) steps 2-4 and (e) step 3
-  const double fl_rk = dn * (4.0 * k * k + 6.0 * k * k);
   LAUNCH(HT_CLASS_RANKK, fl_rk, ht_launch_rankk_right(st, B, ldb, n, s + 1, n - k, k, V, n, w.L1, k, w.T, nb));
-  if (c.want_qz)
+  if (c.want_qz && !ov)
     LAUNCH(HT_CLASS_RANKK, fl_rk, ht_launch_rankk_right(st, Z, ldz, n, s + 1, n - k, k, V, n, w.L1, k, w.T, nb));
   LAUNCH(HT_CLASS_GEMM, fl_gemm(n, k, k),
          ht_gemm(st, 'N', 'T', n, k, k, -1.0, w.Y, n, w.L1, k, 1.0, A + (size_t)(n - k) * lda, lda));
   // partial restore: RQ chain bottom to top (Sec. 3.3.1e); on the emulated path in
   // segments, each followed by the segment's transforms on the rows above its band
   // (emulated sweep) instead of FP64 updates inside the restore kernel
-  const int nbr = ht_num_right_blocks(p, k);
-  const bool seg = w.prec == HT_PREC_EMU && k <= 32;
-  if (nbr > 1) CK(restore_chain(c, 2, p, k, j, w.wyRR, wst, seg));
+  bool waitq = false;  // the deferred Q sweep was launched: the QR restore waits for it
+  if (ov && c.want_qz) {
+    CK(cudaEventRecord(w.side_ev[0], st));
+    CK(cudaStreamWaitEvent(w.side, w.side_ev[0], 0));
+    CK(flush_pendq(c));
+    waitq = true;
+    // Z: (e) step 1 and steps 2-4 of the right reflectors
+    const HtSweepJob jz = {Z, ldz, 1, 0, n, j + 1, 0, 0};
+    LAUNCH_SIDE(fl_sweep(0, p, k, nwr, n, -1, false), run_sweep(c, &jz, 1, w.wyR, wst, 0, p, k, 0, nwr, true));
+    LAUNCH_SIDE(fl_rk, ht_launch_rankk_right(w.side, Z, ldz, n, s + 1, n - k, k, V, n, w.L1, k, w.T, nb));
+  }
+  if (nbr > 1) CK(restore_chain(c, 2, p, k, j, w.wyRR, wst, seg, rs_ctas));
   if (nbr > 1) {
     // rows 0..j of B (on the emulated path already done with the segments),
     // all rows of A and Z, one fused launch
     const HtSweepJob jobs[3] = {{A, lda, 1, 0, n, j + 1, 0, 0},
-                                {Z, ldz, 1, 0, c.want_qz ? n : 0, j + 1, 0, 0},
+                                {Z, ldz, 1, 0, (c.want_qz && !ov) ? n : 0, j + 1, 0, 0},
                                 {B, ldb, 1, 0, seg ? 0 : j + 1, j + 1, 0, 0}};
     const double fl = (seg ? 0.0 : fl_sweep(2, p, k, nbr - 1, j + 1, -1, false)) +
-                      (c.want_qz ? 2.0 : 1.0) * fl_sweep(2, p, k, nbr - 1, n, -1, false);
+                      ((c.want_qz && !ov) ? 2.0 : 1.0) * fl_sweep(2, p, k, nbr - 1, n, -1, false);
     LAUNCH(HT_CLASS_SWEEP, fl, run_sweep(c, jobs, 3, w.wyRR, wst, 2, p, k, 0, nbr - 1));
   }
 
@@ -474,10 +570,10 @@ cudaError_t absorb(Ctx& c, int s, int k) {
   {
     // columns j.. of A and j+1.. of B from the left, all rows of Q from the right, one fused launch
     const HtSweepJob jobs[3] = {{A, lda, 0, j, n - j, j + 1, 0, 0},
-                                {Q, ldq, 1, 0, c.want_qz ? n : 0, j + 1, 0, 0},
+                                {Q, ldq, 1, 0, (c.want_qz && !ov) ? n : 0, j + 1, 0, 0},
                                 {B, ldb, 0, j + 1, p, j + 1, 1, j + 1}};
     const double fl = fl_sweep(1, p, k, nwl, p, 0, true) + fl_sweep(1, p, k, nwl, n - j, -1, true) +
-                      (c.want_qz ? fl_sweep(1, p, k, nwl, n, -1, false) : 0.0);
+                      ((c.want_qz && !ov) ? fl_sweep(1, p, k, nwl, n, -1, false) : 0.0);
     LAUNCH(HT_CLASS_SWEEP, fl, run_sweep(c, jobs, 3, w.wyL, wst, 1, p, k, 0, nwl));
   }
   // U~ = [U1; R~1] (2k x k) in tmp3 with ld 2k
@@ -489,18 +585,35 @@ cudaError_t absorb(Ctx& c, int s, int k) {
          cudaMemcpy2DAsync(Ut + k, 2 * k * sizeof(double), w.R1, k * sizeof(double), k * sizeof(double), k,
                            cudaMemcpyDeviceToDevice, st));
   // (c) steps 4-5, (e) steps 2-3, (d) steps 2-3
-  const double fl_rkl = 8.0 * k * k + 2.0 * k * k;
   LAUNCH(HT_CLASS_RANKK, fl_rkl * p, ht_rankk_left(st, B, ldb, j + 1, p, s + 1, 2 * k, k, Ut, 2 * k, w.S, nb));
   LAUNCH(HT_CLASS_RANKK, fl_rkl * (n - j), ht_rankk_left(st, A, lda, j, n - j, s + 1, 2 * k, k, Ut, 2 * k, w.S, nb));
-  if (c.want_qz)
+  if (c.want_qz && !ov)
     LAUNCH(HT_CLASS_RANKK, fl_rkl * dn, ht_rankk_right_w(st, Q, ldq, n, s + 1, 2 * k, k, Ut, 2 * k, w.S, nb));
-  // (f) restore: QR chain top to bottom (in segments on the emulated path)
-  const int nlb = ht_num_left_blocks(p, k);
-  CK(restore_chain(c, 3, p, k, j, w.wyLR, wst, seg));
+  if (ov && c.want_qz) {
+    CK(cudaEventRecord(w.side_ev[1], st));
+    CK(cudaStreamWaitEvent(w.side, w.side_ev[1], 0));
+    // Q: (d) step 1 of the left reflectors; Z: (e) step 3 (the RQ restore); Q: (d) steps 2-3
+    const HtSweepJob jq = {Q, ldq, 1, 0, n, j + 1, 0, 0};
+    LAUNCH_SIDE(fl_sweep(1, p, k, nwl, n, -1, false), run_sweep(c, &jq, 1, w.wyL, wst, 1, p, k, 0, nwl, true));
+    if (nbr > 1) {
+      const HtSweepJob jz = {Z, ldz, 1, 0, n, j + 1, 0, 0};
+      LAUNCH_SIDE(fl_sweep(2, p, k, nbr - 1, n, -1, false),
+                  run_sweep(c, &jz, 1, w.wyRR, wst, 2, p, k, 0, nbr - 1, true));
+    }
+    LAUNCH_SIDE(fl_rkl * dn, ht_rankk_right_w(w.side, Q, ldq, n, s + 1, 2 * k, k, Ut, 2 * k, w.S, nb));
+    CK(cudaEventRecord(w.side_ev[4], w.side));
+    // (d) step 4, the last Q sweep, goes to the next absorption's RQ window
+    c.pendq = {true, p, k, j, nlb, wst};
+  }
+  // (f) restore: QR chain top to bottom (in segments on the emulated path), after the
+  // deferred Q sweep of the previous absorption has read this store
+  if (waitq) CK(cudaStreamWaitEvent(st, w.side_ev[3], 0));
+  CK(restore_chain(c, 3, p, k, j, w.wyLR, wst, seg, rs_ctas));
   {
-    const HtSweepJob jobs[2] = {{A, lda, 0, j, n - j, j + 1, 0, 0}, {Q, ldq, 1, 0, c.want_qz ? n : 0, j + 1, 0, 0}};
+    const HtSweepJob jobs[2] = {{A, lda, 0, j, n - j, j + 1, 0, 0},
+                                {Q, ldq, 1, 0, (c.want_qz && !ov) ? n : 0, j + 1, 0, 0}};
     const double fl = fl_sweep(3, p, k, nlb, n - j, -1, true) +
-                      (c.want_qz ? fl_sweep(3, p, k, nlb, n, -1, false) : 0.0);
+                      ((c.want_qz && !ov) ? fl_sweep(3, p, k, nlb, n, -1, false) : 0.0);
     LAUNCH(HT_CLASS_SWEEP, fl, run_sweep(c, jobs, 2, w.wyLR, wst, 3, p, k, 0, nlb));
   }
   return cudaGetLastError();
@@ -578,7 +691,8 @@ int ht_reduce_core(HtWork& w, PanelStatus* host_status, unsigned long long* pt_d
   w.ptime = prof.on ? pt_dev : nullptr;
   if (prof.on) cudaMemsetAsync(pt_dev, 0, 32 * sizeof(unsigned long long), st);
   prof.st = st;
-  Ctx c{&w, st, n, A, B, Q, Z, lda, ldb, ldq, ldz, want_qz, 0.0, &prof};
+  prof.side = w.side;
+  Ctx c{&w, st, n, A, B, Q, Z, lda, ldb, ldq, ldz, want_qz, 0.0, &prof, {}};
   cudaEvent_t ev[4] = {};
   const bool timing = (stats != nullptr);
   if (timing)
@@ -599,6 +713,9 @@ int ht_reduce_core(HtWork& w, PanelStatus* host_status, unsigned long long* pt_d
     int s = 0;
     while (s <= n - 3) {
       const int kmax = std::min(nb, (n - s - 1) / 2);
+      // the side stream's Q / Z updates of the previous absorption read the panel's
+      // outputs (V, T, U, S) and the chains' WY stores: join before overwriting them
+      if (w.side && cudaStreamWaitEvent(st, w.side_ev[4], 0) != cudaSuccess) { result = HT_ERR_CUDA; break; }
       if (cudaMemsetAsync(w.status, 0, sizeof(PanelStatus), st) != cudaSuccess) { result = HT_ERR_CUDA; break; }
       if (ht_launch_prepare_B(w, B, ldb, s, seed, 0) != cudaSuccess) { result = HT_ERR_CUDA; break; }
       if (timing) cudaEventRecord(ev[0], st);
@@ -659,6 +776,12 @@ int ht_reduce_core(HtWork& w, PanelStatus* host_status, unsigned long long* pt_d
       s += k;
     }
     if (result != HT_OK) break;
+    if (c.pendq.on && flush_pendq(c) != cudaSuccess) { result = HT_ERR_CUDA; break; }
+    if (w.side && (cudaEventRecord(w.side_ev[4], w.side) != cudaSuccess ||
+                   cudaStreamWaitEvent(st, w.side_ev[4], 0) != cudaSuccess)) {
+      result = HT_ERR_CUDA;
+      break;
+    }
     int derr = 0;
     if (cudaMemcpyAsync(&derr, w.err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
@@ -667,6 +790,11 @@ int ht_reduce_core(HtWork& w, PanelStatus* host_status, unsigned long long* pt_d
     }
     if (derr != 0) result = derr;
   } while (0);
+  if (w.side) {
+    // whatever the outcome, the caller's stream follows every side-stream launch
+    cudaEventRecord(w.side_ev[4], w.side);
+    cudaStreamWaitEvent(st, w.side_ev[4], 0);
+  }
   prof.resolve();
   if (stats && prof.on) {
     unsigned long long pt[24];
@@ -735,6 +863,10 @@ int ht_finalize(void) {
     if (e->busy) {
       keep.push_back(e);
       continue;
+    }
+    if (e->w.side) {
+      for (auto ev : e->w.side_ev) cudaEventDestroy(ev);
+      cudaStreamDestroy(e->w.side);
     }
     cudaFree(e->base);
     cudaFreeHost(e->host_status);

@@ -145,6 +145,16 @@ struct HtWork {
   int* cflags;             // wavefront chains: columns published per window (2 (n + 8) ints)
   int* tc_sched;           // work-unit counters of the tcgen05 sweeps (1 + 3 (n / 128 + 1) ints)
   cudaStream_t stream;
+  // Q / Z updates of an absorption on a second stream (null: all on the caller's
+  // stream), with their own digit buffers and unit counters; side_ev: the main
+  // stream's points the side stream waits for (chains, RQ restore, U-tilde, QR
+  // restore) and [4] the side stream done with the absorption
+  cudaStream_t side;
+  cudaEvent_t side_ev[5];
+  void* emu_dig2;
+  int* emu_exps2;
+  void* emu_geo2;
+  int* tc_sched2;
 };
 #define HT_PART_STRIDE 80   // >= nb + 8 for nb <= 64 ... plus norms
 #define HT_NVEC 8
@@ -175,7 +185,7 @@ cudaError_t ht_launch_form_wy(cudaStream_t st, double* wyR, double* wyL, size_t 
 // step leaves the lines outside ht_restore_band(tb) to a later sweep
 cudaError_t ht_launch_restore(cudaStream_t st, int mode, int p, int k, int j, int n, double* B, long ldb, double* wy,
                               size_t stride, double* tstore, double* taus, int* flag, int* err,
-                              unsigned long long* ptime, long spin, int ta = 0, int tb = -1);
+                              unsigned long long* ptime, long spin, int ta = 0, int tb = -1, int max_ctas = 0);
 int ht_restore_steps(int mode, int p, int k);
 // lines [blo, bhi) (relative to j + 1) that the steps up to tb - 1 still update themselves
 void ht_restore_band(int mode, int p, int k, int tb, int* blo, int* bhi);
@@ -209,11 +219,12 @@ size_t ht_emu_window_bytes(int nb);
 // as ht_sweep_multi with FP64 emulated on the tcgen05 tensor cores (ht_tc.cu):
 // consecutive windows grouped into products of at most 64 x 64, `cap` groups per
 // launch, dig: cap * ht_tc_group_bytes() bytes, exps: cap ints, geo: cap int4,
-// sched: 1 + (line blocks of 128 lines of all jobs) ints of scratch;
+// sched: 1 + (line blocks of 128 lines of all jobs) ints of scratch; at most
+// max_ctas CTAs (0: one per SM);
 // k <= 32; a bounded wait that gives up raises HT_ERR_TIMEOUT in *err
 cudaError_t ht_tc_sweep_multi(cudaStream_t st, const HtSweepJob* jobs, int njobs, const double* wy, long stride,
                               int mode, int p, int k, int t0, int t1, void* dig, int* exps, void* geo, int cap,
-                              int* sched, int* err);
+                              int* sched, int* err, int max_ctas = 0);
 int ht_tc_group(int k);
 size_t ht_tc_group_bytes();
 size_t ht_emu_merge_doubles(int cap);
@@ -228,7 +239,8 @@ cudaError_t ht_rankk_left(cudaStream_t st, double* X, long ldx, int col0, int nc
                           const double* Ut, int ldu, const double* S, int lds);
 int ht_panel_max_ctas(int nb);
 // workspace layout (bytes when b is null) and the driver of Algorithm 1 on it
-size_t ht_layout_work(HtWork& w, char* b, int n, int nb, int G, unsigned long long** pt);
+// side: also the buffers of the side stream's sweeps
+size_t ht_layout_work(HtWork& w, char* b, int n, int nb, int G, unsigned long long** pt, bool side = false);
 int ht_reduce_core(HtWork& w, PanelStatus* host_status, unsigned long long* pt_dev, int n, double* A, int lda,
                    double* B, int ldb, double* Q, int ldq, double* Z, int ldz, int want_qz, int nb, int max_ir,
                    double tol_scale, uint64_t seed, int profile, ht_stats* stats, cudaStream_t st);

@@ -19,6 +19,8 @@
 // X^T: X^T = G [0; R1^T].
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include "ht_common.cuh"
 
 namespace cg = cooperative_groups;
@@ -967,7 +969,7 @@ void ht_restore_band(int mode, int p, int k, int tb, int* blo, int* bhi) {
 
 cudaError_t ht_launch_restore(cudaStream_t st, int mode, int p, int k, int j, int n, double* B, long ldb, double* wy,
                               size_t stride, double* tstore, double* taus, int* flag, int* err,
-                              unsigned long long* ptime, long spin, int ta, int tb) {
+                              unsigned long long* ptime, long spin, int ta, int tb, int max_ctas) {
   set_factor_attr();
   const int nsteps = ht_restore_steps(mode, p, k);
   if (nsteps <= 0) return cudaSuccess;
@@ -985,7 +987,8 @@ cudaError_t ht_launch_restore(cudaStream_t st, int mode, int p, int k, int j, in
     SplitArgs sa{mode, p, k, j, n, B, ldb, wy, stride, tstore, taus, flag, err, ptime, spin > 0 ? spin : HT_SPIN_LIMIT,
                  ta, tb, blo, bhi};
     void* sargs[] = {&sa};
-    return cudaLaunchCooperativeKernel((void*)restore_split_kernel, dim3(sms), dim3(RS_THREADS), sargs,
+    const int g = (max_ctas > RS_FIRST_BULK) ? std::min(sms, max_ctas) : sms;
+    return cudaLaunchCooperativeKernel((void*)restore_split_kernel, dim3(g), dim3(RS_THREADS), sargs,
                                        factor_smem_doubles() * sizeof(double), st);
   }
   RestoreArgs a{mode, p, k, j, n, B, ldb, wy, stride, tstore, ptime};

@@ -752,7 +752,7 @@ size_t ht_tc_group_bytes() { return GD_BYTES; }
 
 cudaError_t ht_tc_sweep_multi(cudaStream_t st, const HtSweepJob* jobs, int njobs, const double* wy, long stride,
                               int mode, int p, int k, int t0, int t1, void* dig, int* exps, void* geo, int cap,
-                              int* sched, int* err) {
+                              int* sched, int* err, int max_ctas) {
   if (njobs < 1 || njobs > HT_SWEEP_MAXJOBS) return cudaErrorInvalidValue;
   if (t1 <= t0) return cudaSuccess;
   if (k < 1 || 2 * k > TW) return cudaErrorNotSupported;
@@ -776,8 +776,9 @@ cudaError_t ht_tc_sweep_multi(cudaStream_t st, const HtSweepJob* jobs, int njobs
   bt.err = err;
   bt.nlb = ctas;
   bt.sched = sched;
-  const int sms = tc_sm_count();
+  int sms = tc_sm_count();
   if (sms <= 0) return cudaErrorUnknown;
+  if (max_ctas > 0) sms = std::min(sms, max_ctas);
   const int g = ht_tc_group(k);
   const int ng = (t1 - t0 + g - 1) / g;
   for (int m0 = 0; m0 < ng; m0 += cap) {
