@@ -514,33 +514,54 @@ __global__ void __launch_bounds__(TTHREADS, 1) tc_sweep_kernel(TcBatch b) {
     bulk_g2s(smem_u32(Gd), b.dig + (size_t)t * (GD_BYTES / 2), GD_BYTES, bar_g);
   }
   g_pending = t < thi;
+  // Xf holds the stripe's columns by absolute index a in slot a mod 64 (a
+  // window spans at most 64 consecutive columns): the columns that the next
+  // window shares stay in shared memory, the others go to X straight from the
+  // read-back, and the next window's new columns are loaded into the freed
+  // slots while this window's products run
+  auto load_cols = [&](int a0, int a1) {
+    const int nc = a1 - a0;
+    if (nc <= 0) return;
+    if (jb.right) {
+      for (int e = tid; e < TM * nc; e += TTHREADS) {
+        const int l = e % TM, a = a0 + e / TM;
+        double* d = Xf + l * XS + (a & (TW - 1));
+        if (l < lines) cp_async8(d, X + (size_t)(lb + l) + (size_t)a * ldx);
+        else *d = 0.0;
+      }
+    } else {
+      for (int e = tid; e < TM * nc; e += TTHREADS) {
+        const int a = a0 + e % nc, l = e / nc;
+        double* d = Xf + l * XS + (a & (TW - 1));
+        if (l < lines) cp_async8(d, X + (size_t)a + (size_t)(lb + l) * ldx);
+        else *d = 0.0;
+      }
+    }
+  };
+  bool first = true;
   while (t < thi) {
     const int4 gq = b.geo[t];
     const int off = gq.x, w = gq.y;
     const int o0 = jb.origin + off;
     const int F = b.exps[t];
-    // ---- stripe -> Xf (line-major), zero beyond w and beyond `lines` ----
-    if (jb.right) {
-      for (int e = tid; e < TM * TW; e += TTHREADS) {
-        const int l = e % TM, c = e / TM;
-        if (l < lines && c < w) cp_async8(Xf + l * XS + c, X + (size_t)(lb + l) + (size_t)(o0 + c) * ldx);
-        else Xf[l * XS + c] = 0.0;
-      }
-    } else {
-      for (int e = tid; e < TM * TW; e += TTHREADS) {
-        const int c = e % TW, l = e / TW;
-        if (l < lines && c < w) cp_async8(Xf + l * XS + c, X + (size_t)(o0 + c) + (size_t)(lb + l) * ldx);
-        else Xf[l * XS + c] = 0.0;
-      }
+    const int tn = next_group(t + 1);
+    int n0 = 0, n1 = 0;  // the next window's columns (none after the unit's last)
+    if (tn < thi) {
+      const int4 gn = b.geo[tn];
+      n0 = jb.origin + gn.x;
+      n1 = n0 + gn.y;
     }
+    if (first) load_cols(o0, o0 + w);
+    first = false;
     cp_async_wait_all();
     __syncthreads();
     // ---- per-line bound over the window, from the four quarters of the line ----
     const int c0 = 16 * cq;
+    auto xval = [&](int c) { return c < w ? Xf[li * XS + ((o0 + c) & (TW - 1))] : 0.0; };
     {
       int em = 1;
 #pragma unroll 8
-      for (int c = 0; c < 16; ++c) em = max(em, expo(Xf[li * XS + c0 + c]));
+      for (int c = 0; c < 16; ++c) em = max(em, expo(xval(c0 + c)));
       Es[cq * TM + li] = em;
     }
     __syncthreads();
@@ -550,7 +571,7 @@ __global__ void __launch_bounds__(TTHREADS, 1) tc_sweep_kernel(TcBatch b) {
     for (int ch = 0; ch < 2; ++ch) {
       uint32_t hb[8][NDX];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) digit_bits<NDX>(to_fixed<0>(Xf[li * XS + c0 + 8 * ch + i], E), hb[i]);
+      for (int i = 0; i < 8; ++i) digit_bits<NDX>(to_fixed<0>(xval(c0 + 8 * ch + i), E), hb[i]);
       const int boff = kmajor_off<TM>(li, c0 + 8 * ch);
 #pragma unroll
       for (int a = 0; a < NDX; ++a) {
@@ -564,6 +585,9 @@ __global__ void __launch_bounds__(TTHREADS, 1) tc_sweep_kernel(TcBatch b) {
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
+    // ---- the next window's new columns into the slots of this one's leaving columns ----
+    load_cols(n0, min(n1, o0));
+    load_cols(max(n0, o0 + w), n1);
     // ---- MMAs: levels 2-5 (groups 0-3), then levels 6-7 (groups 4-7) ----
     // A: 128 lines, K chunks 2048 bytes apart; B: 64 output columns, K chunks 1024 apart
     const uint64_t da = sdesc(smem_u32(Xd), TM * 16, 128), db = sdesc(smem_u32(Gd), TW * 16, 128);
@@ -642,7 +666,12 @@ __global__ void __launch_bounds__(TTHREADS, 1) tc_sweep_kernel(TcBatch b) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           tot[i] += (t78[i] + (1LL << 14)) >> 15;
-          Xf[li * XS + 16 * cq + i] = scaled_double(tot[i], ex);
+          const int c = 16 * cq + i, a = o0 + c;
+          if (c >= w) continue;
+          const double v = scaled_double(tot[i], ex);
+          if (a >= n0 && a < n1) Xf[li * XS + (a & (TW - 1))] = v;  // shared with the next window
+          else if (li < lines)
+            X[jb.right ? (size_t)(lb + li) + (size_t)a * ldx : (size_t)a + (size_t)(lb + li) * ldx] = v;
         }
       }
     }
@@ -654,25 +683,11 @@ __global__ void __launch_bounds__(TTHREADS, 1) tc_sweep_kernel(TcBatch b) {
     g_pending = false;
     if (tid == 0) *m2_issued = 0;
     // ---- prefetch the next group's digits (all MMAs of this one are done) ----
-    const int tn = next_group(t + 1);
     if (tid == 0 && tn < thi) {
       mbar_expect_tx(bar_g, GD_BYTES);
       bulk_g2s(smem_u32(Gd), b.dig + (size_t)tn * (GD_BYTES / 2), GD_BYTES, bar_g);
     }
     g_pending = tn < thi;
-    // ---- Xf -> stripe ----
-    if (jb.right) {
-      for (int e = tid; e < TM * TW; e += TTHREADS) {
-        const int l = e % TM, c = e / TM;
-        if (l < lines && c < w) X[(size_t)(lb + l) + (size_t)(o0 + c) * ldx] = Xf[l * XS + c];
-      }
-    } else {
-      for (int e = tid; e < TM * TW; e += TTHREADS) {
-        const int c = e % TW, l = e / TW;
-        if (l < lines && c < w) X[(size_t)(o0 + c) + (size_t)(lb + l) * ldx] = Xf[l * XS + c];
-      }
-    }
-    __syncthreads();
     phase ^= 1u;
     t = tn;
   }
@@ -684,6 +699,7 @@ __global__ void __launch_bounds__(TTHREADS, 1) tc_sweep_kernel(TcBatch b) {
   }
   }
   // ---- clean-up: after a timeout, wait (bounded) for what is in flight ----
+  cp_async_wait_all();
   if (*abort_flag && tid == 0) {
     if (g_pending) mbar_wait(bar_g, phase);
     if (m_pending) {
