@@ -94,12 +94,10 @@ size_t ht_layout_work(HtWork& w, char* b, int n, int nb, int G, unsigned long lo
   const size_t oTst = take(nn * nb + 4 * (size_t)nb * nb);  // (p/k + 1) T factors of k^2 each
   const size_t oWpart = take((size_t)((n + HT_TRMV_CW - 1) / HT_TRMV_CW + 1) * nn);
   // digits of the emulated sweeps: windows of a chain are processed in launches of emu_cap windows
-  const size_t emu_win = nb <= 32 ? ht_emu_window_bytes(nb) : 0;
+  const size_t emu_win = nb <= 32 ? ht_tc_group_bytes() : 0;
   w.emu_cap = std::min(n / 32 + 4, 1024);
   const size_t oEmu = take(emu_win ? (emu_win * w.emu_cap + sizeof(double) - 1) / sizeof(double) : 0);
   const size_t oEmuE = take((size_t)w.emu_cap);
-  // merged windows of the emulated sweeps of chains with k <= 16
-  const size_t oEmuM = take(ht_emu_merge_doubles(w.emu_cap));
   const size_t oEmuG = take(2 * (size_t)w.emu_cap);  // int4 = 2 doubles
   const size_t oCf = take((size_t)n + 8);  // 2 (n + 8) ints
   const size_t oRc = take(2);
@@ -142,7 +140,6 @@ size_t ht_layout_work(HtWork& w, char* b, int n, int nb, int G, unsigned long lo
   w.nearv = (double*)(b + oNear);
   w.emu_dig = emu_win ? (void*)(b + oEmu) : nullptr;
   w.emu_exps = (int*)(b + oEmuE);
-  w.emu_mwy = (double*)(b + oEmuM);
   w.emu_geo = (void*)(b + oEmuG);
   w.rcount = (int*)(b + oRc);
   w.cflags = (int*)(b + oCf);
@@ -367,12 +364,9 @@ cudaError_t run_sweep(Ctx& c, const HtSweepJob* jobs, int njobs, const double* w
     return ht_tc_sweep_multi(c.w->side, jobs, njobs, wy, wst, mode, p, k, t0, t1, c.w->emu_dig2, c.w->emu_exps2,
                              c.w->emu_geo2, c.w->emu_cap, c.w->tc_sched2, c.w->err, side_ctas());
   }
-  if (c.w->prec == HT_PREC_EMU && c.w->tc)
+  if (c.w->prec == HT_PREC_EMU)
     return ht_tc_sweep_multi(c.st, jobs, njobs, wy, wst, mode, p, k, t0, t1, c.w->emu_dig, c.w->emu_exps,
                              c.w->emu_geo, c.w->emu_cap, c.w->tc_sched, c.w->err);
-  if (c.w->prec == HT_PREC_EMU)
-    return ht_emu_sweep_multi(c.st, jobs, njobs, wy, wst, mode, p, k, t0, t1, c.w->emu_dig, c.w->emu_exps,
-                              c.w->emu_cap, c.w->emu_mwy, c.w->emu_geo);
   // the FP64 sweeps take the windows one by one: they are DFMA-bound, and a merged window
   // of g windows multiplies their flops by about g / 2
   return ht_sweep_multi(c.st, jobs, njobs, wy, wst, mode, p, k, t0, t1);
@@ -509,7 +503,7 @@ cudaError_t absorb(Ctx& c, int s, int k) {
   const int nbr = ht_num_right_blocks(p, k);
   const int nlb = ht_num_left_blocks(p, k);
   const bool seg = w.prec == HT_PREC_EMU && k <= 32;
-  const bool ov = seg && w.side && w.tc;
+  const bool ov = seg && w.side;
   const int rs_ctas = ov ? RS_MAIN_CTAS : 0;
   const double fl_rk = dn * (4.0 * k * k + 6.0 * k * k);
   const double fl_rkl = 8.0 * k * k + 2.0 * k * k;
@@ -670,7 +664,6 @@ int reduce_impl(int n, double* A, int lda, double* B, int ldb, double* Q, int ld
   if (!pe) return rc;
   pe->w.prec = prec;
   pe->w.spin = (opt && opt->wait_polls > 0) ? (long)opt->wait_polls : (long)HT_SPIN_LIMIT;
-  pe->w.tc = (opt && opt->reserved[0]) ? 0 : 1;
   const int result = ht_reduce_core(pe->w, pe->host_status, pe->pt_dev, n, A, lda, B, ldb, Q, ldq, Z, ldz, want_qz,
                                     nb, max_ir, tol_scale, seed, opt && opt->profile, stats, st);
   release(pe);

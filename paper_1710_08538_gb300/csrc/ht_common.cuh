@@ -134,14 +134,12 @@ struct HtWork {
   double* tstore;          // T factors of the restore steps (HT_NB_MAX^2 each)
   int* rcount;             // restore: reflectors published (a step-stamped counter)
   double* rtaus;           // tau of every restore step (n + 2 HT_NB_MAX)
-  void* emu_dig;           // digits of Vw / Ww for the emulated sweeps (emu_cap windows)
-  int* emu_exps;           // their exponent bounds (2 per window)
-  double* emu_mwy;         // merged windows of small-k chains (ht_emu_merge_doubles(emu_cap))
+  void* emu_dig;           // digits of the grouped window transforms of the emulated sweeps (emu_cap groups)
+  int* emu_exps;           // their exponent bounds (one per group)
   void* emu_geo;           // their table (emu_cap int4)
   int emu_cap;             // windows per launch of the emulated sweeps
   int prec;                // HT_PREC_* of the current call
   long spin;               // polls before a bounded device wait gives up (HT_SPIN_LIMIT by default)
-  int tc;                  // emulated sweeps on tcgen05 (ht_tc.cu) instead of mma.sync (ht_emu.cu)
   int* cflags;             // wavefront chains: columns published per window (2 (n + 8) ints)
   int* tc_sched;           // work-unit counters of the tcgen05 sweeps (1 + 3 (n / 128 + 1) ints)
   cudaStream_t stream;
@@ -203,19 +201,6 @@ struct HtSweepJob {
 };
 cudaError_t ht_sweep_multi(cudaStream_t st, const HtSweepJob* jobs, int njobs, const double* wy, long stride, int mode,
                            int p, int k, int t0, int t1);
-// products of g consecutive window transforms of windows [ta, tb) of a chain
-// (mode 0-3), one merged window per g: V', W' at mwy + m * ht_merge_stride()
-// (W' at + ht_merge_stride() / 2) and the int4 table geo[m] (ht_emu.cu)
-cudaError_t ht_merge_windows(cudaStream_t st, const double* wy, long stride, int mode, int p, int k, int g, int ta,
-                             int tb, double* mwy, void* geo);
-long ht_merge_stride();
-// as ht_sweep_multi with FP64 emulated on the tensor cores (ht_emu.cu); needs
-// k <= 32, a digit buffer of `cap` windows of ht_emu_window_bytes(k) each and,
-// to merge the windows of chains with k <= 16, ht_emu_merge_doubles(cap)
-// doubles at mwy and cap int4 at geo (null: no merging)
-cudaError_t ht_emu_sweep_multi(cudaStream_t st, const HtSweepJob* jobs, int njobs, const double* wy, long stride, int mode,
-                               int p, int k, int t0, int t1, void* dig, int* exps, int cap, double* mwy, void* geo);
-size_t ht_emu_window_bytes(int nb);
 // as ht_sweep_multi with FP64 emulated on the tcgen05 tensor cores (ht_tc.cu):
 // consecutive windows grouped into products of at most 64 x 64, `cap` groups per
 // launch, dig: cap * ht_tc_group_bytes() bytes, exps: cap ints, geo: cap int4,
@@ -227,7 +212,6 @@ cudaError_t ht_tc_sweep_multi(cudaStream_t st, const HtSweepJob* jobs, int njobs
                               int* sched, int* err, int max_ctas = 0);
 int ht_tc_group(int k);
 size_t ht_tc_group_bytes();
-size_t ht_emu_merge_doubles(int cap);
 cudaError_t ht_sweep(cudaStream_t st, int right, double* X, long ldx, int line0, int nlines, int origin,
                      const double* wy, long stride, int mode, int p, int k, int t0, int t1, int use_limit,
                      int limit_base);
