@@ -1,21 +1,25 @@
-"""Merged windows of the emulated chain applications (chains with k <= 16).
+"""Grouped windows of the emulated chain applications (tcgen05 sweep).
 
-The emulated sweeps apply the product of g = floor(32 / k) consecutive window
-transforms of a chain (Sec. 3.3, Remark 3.2) as one block on the union of their
-rows.  The merge kernel keeps that block in fixed shared-memory tiles of 64 rows
-and 32 columns, and it assumes the union is contiguous.  These CPU tests check
-both assumptions against the window geometry of the oracle (written from the
-paper independently of the CUDA path), for every chain kind.  They also check
-the composition rule
-    (I - V1 W1^T)(I - V2 W2^T) = I - [V1, V2 - V1 (W1^T V2)] [W1, W2]^T
-on random chains of Householder windows.
+The emulated sweeps apply the product G = G_t0 G_t0+1 ... of g = max(1, 64/k - 1)
+consecutive window transforms of a chain (Sec. 3.3, Remark 3.2) as one dense
+product on the union of their rows.  The sweep kernel holds G and a stripe of
+lines in fixed 64-wide tiles, and it assumes the union is contiguous.  These
+CPU tests check both assumptions against the window geometry of the oracle
+(written from the paper independently of the CUDA path), for every chain kind
+and k <= 32.  They also check that applying the group's product once equals
+applying its windows one by one, on random chains of Householder windows.
 """
 import numpy as np
 import pytest
 
 from oracle import househt as hh
 
-MROWS, MCOLS = 64, 32
+TW = 64  # widest group (rows of the union) of the sweep kernel
+
+
+def group(k):
+    """Windows per group of the tcgen05 sweep for chains of k reflectors."""
+    return max(1, TW // k - 1)
 
 
 def chain_windows(kind, p, k):
@@ -43,17 +47,16 @@ def chain_windows(kind, p, k):
 
 
 @pytest.mark.parametrize("kind", [0, 1, 2, 3])
-@pytest.mark.parametrize("k", list(range(1, 17)))
-def test_merged_window_fits_the_tiles(kind, k):
-    g = 32 // k
+@pytest.mark.parametrize("k", list(range(1, 33)))
+def test_group_fits_the_tiles(kind, k):
+    g = group(k)
     for p in list(range(1, 200)) + [257, 1000, 4093, 16382]:
         wins = chain_windows(kind, p, k)
         for m0 in range(0, len(wins), g):
             grp = wins[m0:m0 + g]
             lo = min(o for o, _, _ in grp)
             hi = max(o + w for o, w, _ in grp)
-            cols = sum(r for _, _, r in grp)
-            assert hi - lo <= MROWS and cols <= MCOLS, (kind, k, p, m0, hi - lo, cols)
+            assert hi - lo <= TW, (kind, k, p, m0, hi - lo)
             # contiguous union: every row of [lo, hi) is in some window
             covered = np.zeros(hi - lo, dtype=bool)
             for o, w, _ in grp:
@@ -82,11 +85,11 @@ def _householder_window(rng, w, k):
     return V, V @ T.T
 
 
-@pytest.mark.parametrize("k", [1, 2, 3, 7, 16])
-def test_merge_rule_reproduces_the_chain(k):
+@pytest.mark.parametrize("k", [1, 2, 3, 7, 16, 21, 32])
+def test_group_product_reproduces_the_chain(k):
     rng = np.random.default_rng(100 + k)
     p = 23 * k + 5
-    g = 32 // k
+    g = group(k)
     wins = [(o, w, _householder_window(rng, w, r)) for o, w, r in chain_windows(0, p, k) if r <= w]
     X = rng.standard_normal((7, p))
     ref = X.copy()
@@ -98,15 +101,10 @@ def test_merge_rule_reproduces_the_chain(k):
         grp = wins[m0:m0 + g]
         lo = min(o for o, _, _ in grp)
         hi = max(o + w for o, w, _ in grp)
-        Va = np.zeros((hi - lo, 0))
-        Wa = np.zeros((hi - lo, 0))
+        G = np.eye(hi - lo)
         for o, w, (V, W) in grp:
-            Ve = np.zeros((hi - lo, V.shape[1]))
-            We = np.zeros((hi - lo, V.shape[1]))
-            Ve[o - lo:o - lo + w] = V
-            We[o - lo:o - lo + w] = W
-            Va = np.hstack([Va, Ve - Va @ (Wa.T @ Ve)])
-            Wa = np.hstack([Wa, We])
-        seg = got[:, lo:hi]
-        got[:, lo:hi] = seg - (seg @ Va) @ Wa.T
+            Gi = np.eye(hi - lo)
+            Gi[o - lo:o - lo + w, o - lo:o - lo + w] -= V @ W.T
+            G = G @ Gi
+        got[:, lo:hi] = got[:, lo:hi] @ G
     assert np.max(np.abs(got - ref)) <= 1e-13 * max(1.0, np.max(np.abs(ref)))
