@@ -78,6 +78,10 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=1024)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--config", default="single", choices=["single", "batch"],
+                   help="single: the headline pencil; batch: 512 pencils n ~ U{64..1024} in one "
+                        "ht_reduce_batched call against a loop of ht_reduce calls (not the headline)")
+    p.add_argument("--batch-count", type=int, default=512)
     p.add_argument("--budget", type=float, default=1650.0,
                    help="wall-clock seconds the whole run must fit; fewer warm-up, then timed, steps if needed")
     return p.parse_args()
@@ -428,9 +432,75 @@ def run_ours(args):
         sys.exit(1)
 
 
+def run_batch(args):
+    """The batched workload: `batch-count` pencils of orders drawn uniformly
+    from 64..1024 (A ~ N(0,1), B = R of the QR of an N(0,1) matrix), FP64 with
+    Q and Z; the time of one ht_reduce_batched call against a loop of ht_reduce
+    calls on the same resident inputs (W untimed warm-up calls of each first),
+    and the invariants of a sample of the batched results."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_1710_08538_gb300 as ht
+    from paper_1710_08538_gb300 import check, pencils
+    dev = torch.device("cuda", 0)
+    sizes = [int(x) for x in pencils.batch_sizes(args.batch_count, args.seed)]
+    host = [pencils.random_qr(n, args.seed + 1 + i) for i, n in enumerate(sizes)]
+    A0 = [ht.colmajor(A) for A, _ in host]
+    B0 = [ht.colmajor(B) for _, B in host]
+    As = [torch.empty_like(a) for a in A0]
+    Bs = [torch.empty_like(b) for b in B0]
+    Qs = [torch.empty_like(a) for a in A0]
+    Zs = [torch.empty_like(a) for a in A0]
+
+    def reset():
+        for a, b, a0, b0 in zip(As, Bs, A0, B0):
+            a.copy_(a0)
+            b.copy_(b0)
+        torch.cuda.synchronize(dev)
+
+    def timed(fn):
+        reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / 1e3
+
+    def batched():
+        ht.reduce_batched(As, Bs, Qs, Zs)
+
+    def loop():
+        for a, b, q, z in zip(As, Bs, Qs, Zs):
+            ht.reduce(a, b, q, z)
+
+    for _ in range(max(1, args.warmup)):
+        timed(batched)
+    t_batch = min(timed(batched) for _ in range(max(1, args.steps)))
+    reps = []
+    for i in range(0, len(sizes), max(1, len(sizes) // 8)):
+        reps.append(check.invariants(A0[i], B0[i], As[i], Bs[i], Qs[i], Zs[i], probes=8, seed=7))
+    t_loop = timed(loop)  # every order's workspace already exists (the batched calls made them)
+    flops = sum(116.0 * n ** 3 / 3.0 for n in sizes)
+    ok = all(r["h_nonzeros_below_subdiag"] == 0 and r["t_nonzeros_below_diag"] == 0 and
+             max(r["bwd_a"], r["bwd_b"]) <= 20 * r["n"] * 2.0 ** -52 for r in reps)
+    print(json.dumps({
+        "metric": "s per batch (512 pencils, n ~ U{64..1024}, FP64, Q and Z)", "value": t_batch, "unit": "s",
+        "higher_is_better": False, "config": {"workload": f"{len(sizes)} pencils, A ~ N(0,1), B = R of QR(N(0,1)), "
+                                                          f"orders {min(sizes)}..{max(sizes)}", "sum_n3": float(sum(n ** 3 for n in sizes))},
+        "batched_s": t_batch, "loop_s": t_loop, "speedup_vs_loop": t_loop / t_batch,
+        "batched_tflops": flops / t_batch / 1e12, "invariants_ok_on_sample": ok,
+        "sample_bwd_max": max(max(r["bwd_a"], r["bwd_b"]) for r in reps),
+        "dtype": "f64", "data": "synthetic", "n_gpus": 1}), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.config == "batch" and a.impl == "ours":
+        run_batch(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

@@ -11,6 +11,8 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <thread>
+#include <atomic>
 #include <vector>
 
 #include "ht_common.cuh"
@@ -41,6 +43,7 @@ void set_stream_status(cudaStream_t st, int v) {
 // ---------------------------------------------------------------------------
 struct PoolEntry {
   int dev, n, nb;
+  int G;                      // CTAs of the cooperative panel on the whole GPU
   bool busy;
   HtWork w;
   void* base;
@@ -168,6 +171,7 @@ int alloc_work(PoolEntry* e, int n, int nb) {
   cudaMemset(base, 0, total);
   ht_layout_work(w, (char*)base, n, nb, G, &e->pt_dev, true);
   e->base = base;
+  e->G = G;
   // the side stream of the Q / Z updates and its events (without them, one stream)
   if (cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking) != cudaSuccess) {
     w.side = nullptr;
@@ -346,6 +350,8 @@ double fl_sweep(int mode, int p, int k, int nwin, double lines, int limit_base, 
 // restore launches take at most RS_MAIN_CTAS CTAs, the side stream's sweeps the
 // other SMs, so that both are resident together whatever runs first.
 constexpr int RS_MAIN_CTAS = 88;
+// CTAs per lane of ht_reduce_batched (at least the restore kernel's 20 roles)
+constexpr int BATCH_LANE_CTAS = 38;
 int sm_count() {
   static int sms[64] = {};
   int dev = 0;
@@ -366,7 +372,7 @@ cudaError_t run_sweep(Ctx& c, const HtSweepJob* jobs, int njobs, const double* w
   }
   if (c.w->prec == HT_PREC_EMU)
     return ht_tc_sweep_multi(c.st, jobs, njobs, wy, wst, mode, p, k, t0, t1, c.w->emu_dig, c.w->emu_exps,
-                             c.w->emu_geo, c.w->emu_cap, c.w->tc_sched, c.w->err);
+                             c.w->emu_geo, c.w->emu_cap, c.w->tc_sched, c.w->err, c.w->cap);
   // the FP64 sweeps take the windows one by one: they are DFMA-bound, and a merged window
   // of g windows multiplies their flops by about g / 2
   return ht_sweep_multi(c.st, jobs, njobs, wy, wst, mode, p, k, t0, t1);
@@ -411,7 +417,7 @@ cudaError_t restore_chain(Ctx& c, int mode, int p, int k, int j, double* wy, lon
   if (!seg) {
     LAUNCH(HT_CLASS_RESTORE, fl_restore(mode, p, k, 0, nsteps, 0, p),
            ht_launch_restore(c.st, mode, p, k, j, c.n, c.B, c.ldb, wy, wst, w.tstore, w.rtaus, w.rcount, w.err,
-                             w.ptime, w.spin));
+                             w.ptime, w.spin, 0, -1, max_ctas));
     return cudaSuccess;
   }
   for (int ta = 0; ta < nsteps; ta += RS_SEG) {
@@ -488,7 +494,7 @@ cudaError_t absorb(Ctx& c, int s, int k) {
   if (k <= 32)
     LAUNCH(HT_CLASS_CHAIN_FACTOR, 2.0 * fl_chain(p, k),
            ht_launch_chains_wave(st, V + k, w.U2w, n, p, k, w.wyR, w.wyL, wst, w.L1, w.R1, w.tmp1, w.tmp3, w.cflags,
-                                 w.err, w.spin));
+                                 w.err, w.spin, w.cap));
   else
     LAUNCH(HT_CLASS_CHAIN_FACTOR, 2.0 * fl_chain(p, k),
            ht_launch_chains(st, V + k, w.U2w, n, p, k, w.wyR, w.wyL, wst, w.L1, w.R1));
@@ -503,8 +509,8 @@ cudaError_t absorb(Ctx& c, int s, int k) {
   const int nbr = ht_num_right_blocks(p, k);
   const int nlb = ht_num_left_blocks(p, k);
   const bool seg = w.prec == HT_PREC_EMU && k <= 32;
-  const bool ov = seg && w.side;
-  const int rs_ctas = ov ? RS_MAIN_CTAS : 0;
+  const bool ov = seg && w.side && w.cap == 0;
+  const int rs_ctas = ov ? RS_MAIN_CTAS : w.cap;
   const double fl_rk = dn * (4.0 * k * k + 6.0 * k * k);
   const double fl_rkl = 8.0 * k * k + 2.0 * k * k;
   // (c)-(e) step 1: A, Z, B columns j+1..n-1 times the chain, one fused launch
@@ -628,7 +634,7 @@ int check_args(int n, const void* A, int lda, const void* B, int ldb, const void
 }
 
 int reduce_impl(int n, double* A, int lda, double* B, int ldb, double* Q, int ldq, double* Z, int ldz, int want_qz,
-                const ht_options* opt, ht_stats* stats, cudaStream_t st) {
+                const ht_options* opt, ht_stats* stats, cudaStream_t st, int cap = 0) {
   int rc = check_args(n, A, lda, B, ldb, Q, ldq, Z, ldz, want_qz);
   if (rc != HT_OK) return rc;
   int nb = 32, max_ir = 10, prec = HT_PREC_FP64;
@@ -663,6 +669,8 @@ int reduce_impl(int n, double* A, int lda, double* B, int ldb, double* Q, int ld
   PoolEntry* pe = acquire(n, nb, &rc);
   if (!pe) return rc;
   pe->w.prec = prec;
+  pe->w.cap = cap;
+  pe->w.G = cap > 0 ? std::min(pe->G, cap) : pe->G;
   pe->w.spin = (opt && opt->wait_polls > 0) ? (long)opt->wait_polls : (long)HT_SPIN_LIMIT;
   const int result = ht_reduce_core(pe->w, pe->host_status, pe->pt_dev, n, A, lda, B, ldb, Q, ldq, Z, ldz, want_qz,
                                     nb, max_ir, tol_scale, seed, opt && opt->profile, stats, st);
@@ -828,16 +836,67 @@ int ht_reduce_batched(int batch, const int* n, double* const* A, const int* lda,
   if (batch < 0) return -1;
   if (batch > 0 && (!n || !A || !lda || !B || !ldb)) return -2;
   if (want_qz && batch > 0 && (!Q || !Z)) return -7;
+  if (batch == 0) return HT_OK;
   std::vector<int> order(batch);
   for (int i = 0; i < batch; ++i) order[i] = i;
   std::sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
-  for (int i : order) {
-    const int rc = reduce_impl(n[i], A[i], lda[i], B[i], ldb[i], want_qz ? Q[i] : nullptr, std::max(1, n[i]),
-                               want_qz ? Z[i] : nullptr, std::max(1, n[i]), want_qz, nullptr, nullptr,
-                               (cudaStream_t)stream);
-    if (rc != HT_OK) return rc;
+  cudaStream_t user = (cudaStream_t)stream;
+  auto one = [&](int i, cudaStream_t st, int cap) {
+    return reduce_impl(n[i], A[i], lda[i], B[i], ldb[i], want_qz ? Q[i] : nullptr, std::max(1, n[i]),
+                       want_qz ? Z[i] : nullptr, std::max(1, n[i]), want_qz, nullptr, nullptr, st, cap);
+  };
+  // Lanes: the pencils are independent, and one reduction of a small pencil
+  // leaves most of the GPU idle (its panels and restore chains are latency-
+  // bound), so BATCH_LANES host threads each reduce pencils, largest first, on
+  // a stream of their own.  Every launch of a lane whose CTAs wait on one
+  // another takes at most sms / lanes CTAs, so that those of all lanes are
+  // resident together.
+  const int sms = sm_count();
+  const int lanes = std::min(batch, std::max(1, sms / BATCH_LANE_CTAS));
+  if (lanes <= 1) {
+    for (int i : order) {
+      const int rc = one(i, user, 0);
+      if (rc != HT_OK) return rc;
+    }
+    return HT_OK;
   }
-  return HT_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HT_ERR_CUDA;
+  const int cap = sms / lanes;
+  std::vector<cudaStream_t> ls(lanes, nullptr);
+  std::vector<cudaEvent_t> le(lanes + 1, nullptr);
+  int rc = HT_OK;
+  for (int l = 0; l < lanes && rc == HT_OK; ++l)
+    if (cudaStreamCreateWithFlags(&ls[l], cudaStreamNonBlocking) != cudaSuccess) rc = HT_ERR_CUDA;
+  for (int l = 0; l <= lanes && rc == HT_OK; ++l)
+    if (cudaEventCreateWithFlags(&le[l], cudaEventDisableTiming) != cudaSuccess) rc = HT_ERR_CUDA;
+  // the lanes start after the caller's earlier work on `stream`
+  if (rc == HT_OK && cudaEventRecord(le[lanes], user) != cudaSuccess) rc = HT_ERR_CUDA;
+  for (int l = 0; l < lanes && rc == HT_OK; ++l)
+    if (cudaStreamWaitEvent(ls[l], le[lanes], 0) != cudaSuccess) rc = HT_ERR_CUDA;
+  if (rc == HT_OK) {
+    std::atomic<int> next{0}, err{HT_OK};
+    std::vector<std::thread> th;
+    for (int l = 0; l < lanes; ++l)
+      th.emplace_back([&, l]() {
+        if (cudaSetDevice(dev) != cudaSuccess) { int z = HT_OK; err.compare_exchange_strong(z, HT_ERR_CUDA); return; }
+        for (;;) {
+          const int q = next.fetch_add(1);
+          if (q >= batch || err.load() != HT_OK) return;
+          const int r = one(order[q], ls[l], cap);
+          if (r != HT_OK) { int z = HT_OK; err.compare_exchange_strong(z, r); return; }
+        }
+      });
+    for (auto& t : th) t.join();
+    rc = err.load();
+    // the caller's stream follows every lane
+    for (int l = 0; l < lanes; ++l)
+      if (cudaEventRecord(le[l], ls[l]) != cudaSuccess || cudaStreamWaitEvent(user, le[l], 0) != cudaSuccess)
+        rc = (rc == HT_OK) ? HT_ERR_CUDA : rc;
+  }
+  for (auto s2 : ls) if (s2) cudaStreamDestroy(s2);
+  for (auto e2 : le) if (e2) cudaEventDestroy(e2);
+  return rc;
 }
 
 int ht_last_device_status(ht_stream_t stream, int* status) {

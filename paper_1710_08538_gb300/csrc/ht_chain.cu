@@ -242,7 +242,7 @@ constexpr int CHAIN_SMEM = (3 * CW_MAX * CK_MAX + 2 * CK_MAX + 8) * (int)sizeof(
 // doubles, flags: two arrays of nwin ints.
 cudaError_t ht_launch_chains_wave(cudaStream_t st, double* V2, double* U2, long ld, int p, int k, double* wyR,
                                   double* wyL, size_t stride, double* L1, double* R1, double* pubR, double* pubL,
-                                  int* flags, int* err, long spin) {
+                                  int* flags, int* err, long spin, int max_ctas) {
   if (k < 1 || k > CK_MAX) return cudaErrorNotSupported;
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -261,7 +261,8 @@ cudaError_t ht_launch_chains_wave(cudaStream_t st, double* V2, double* U2, long 
   e = cudaMemsetAsync(flags, 0, 2 * (size_t)nwin * sizeof(int), st);
   if (e != cudaSuccess) return e;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int G2 = std::max(1, std::min(sms / 2, nwin));
+  int G2 = std::max(1, std::min(sms / 2, nwin));
+  if (max_ctas >= 2) G2 = std::min(G2, max_ctas / 2);
   ChainArgs a;
   a.X[0] = V2; a.X[1] = U2; a.ld = ld; a.p = p; a.k = k;
   a.wy[0] = wyR; a.wy[1] = wyL; a.stride = stride;

@@ -149,6 +149,10 @@ struct HtWork {
   // restore) and [4] the side stream done with the absorption
   cudaStream_t side;
   cudaEvent_t side_ev[5];
+  // at most this many CTAs (0: the whole GPU) for every launch whose CTAs wait on
+  // one another (cooperative panel, chains and restore; the tcgen05 sweeps), so
+  // that reductions on concurrent streams are all resident together
+  int cap;
   void* emu_dig2;
   int* emu_exps2;
   void* emu_geo2;
@@ -176,7 +180,7 @@ cudaError_t ht_launch_chains(cudaStream_t st, double* V2, double* U2, long ld, i
 // pubR, pubL hold p k doubles each, flags 2 (p / k + 2) ints; then T / Ww
 cudaError_t ht_launch_chains_wave(cudaStream_t st, double* V2, double* U2, long ld, int p, int k, double* wyR,
                                   double* wyL, size_t stride, double* L1, double* R1, double* pubR, double* pubL,
-                                  int* flags, int* err, long spin);
+                                  int* flags, int* err, long spin, int max_ctas = 0);
 cudaError_t ht_launch_form_wy(cudaStream_t st, double* wyR, double* wyL, size_t stride, int p, int k);
 // restore chain of B (mode 2: RQ right, mode 3: QR left), one cooperative launch
 // steps [ta, tb) of it (tb < 0: to the end); a launch that ends before the last

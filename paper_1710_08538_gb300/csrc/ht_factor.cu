@@ -993,6 +993,7 @@ cudaError_t ht_launch_restore(cudaStream_t st, int mode, int p, int k, int j, in
   }
   RestoreArgs a{mode, p, k, j, n, B, ldb, wy, stride, tstore, ptime};
   void* args[] = {&a};
-  return cudaLaunchCooperativeKernel((void*)restore_kernel, dim3(sms), dim3(HT_THREADS), args,
+  const int g = max_ctas > 0 ? std::min(sms, max_ctas) : sms;
+  return cudaLaunchCooperativeKernel((void*)restore_kernel, dim3(g), dim3(HT_THREADS), args,
                                      factor_smem_doubles() * sizeof(double), st);
 }

@@ -187,6 +187,39 @@ def test_batched_matches_single(ht):
         checks.assert_invariants(A, B, dA.cpu().numpy(), dB.cpu().numpy(), dQ.cpu().numpy(), dZ.cpu().numpy())
 
 
+def test_batched_lanes_match_single_calls(ht):
+    """Twelve pencils of uneven order (up to 700) in one ht_reduce_batched
+    call.  The batch runs on concurrent lanes (host threads with streams of
+    their own, each launch whose CTAs wait on one another capped at a share of
+    the SMs: the panel then takes the grid-synchronous solve), and gives the
+    results of one ht_reduce call per pencil, elementwise after sign
+    normalisation, and the invariants."""
+    sizes = [700, 3, 129, 450, 64, 257, 333, 96, 511, 5, 200, 640]
+    As, Bs, Qs, Zs, refs = [], [], [], [], []
+    for i, n in enumerate(sizes):
+        A, B = pencils.random_qr(n, 1900 + i)
+        refs.append((A, B))
+        As.append(ht.colmajor(A)); Bs.append(ht.colmajor(B))
+        Qs.append(ht.colmajor(np.zeros((n, n)))); Zs.append(ht.colmajor(np.zeros((n, n))))
+    ht.reduce_batched(As, Bs, Qs, Zs)
+    torch.cuda.synchronize()
+    for (A, B), dA, dB, dQ, dZ in zip(refs, As, Bs, Qs, Zs):
+        got = [x.cpu().numpy() for x in (dA, dB, dQ, dZ)]
+        checks.assert_invariants(A, B, *got)
+        n = A.shape[0]
+        if n <= 2:
+            continue
+        sA, sB = ht.colmajor(A), ht.colmajor(B)
+        sQ, sZ = ht.colmajor(np.zeros((n, n))), ht.colmajor(np.zeros((n, n)))
+        ht.reduce(sA, sB, sQ, sZ)
+        torch.cuda.synchronize()
+        ref = checks.sign_normalize(*[x.cpu().numpy() for x in (sA, sB, sQ, sZ)])
+        gotn = checks.sign_normalize(*got)
+        for name, a, b in zip("HTQZ", ref, gotn):
+            err = float(np.max(np.abs(a - b)))
+            assert err <= 1e-10 * max(1.0, float(np.max(np.abs(a)))), (n, name, err)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "emu"])
 def test_elementwise_vs_algorithm1_three_solve_blocks(ht, prec):
     """n = 600: the trailing system has up to 599 rows, so the look-ahead
