@@ -351,7 +351,7 @@ double fl_sweep(int mode, int p, int k, int nwin, double lines, int limit_base, 
 // other SMs, so that both are resident together whatever runs first.
 constexpr int RS_MAIN_CTAS = 88;
 // CTAs per lane of ht_reduce_batched (at least the restore kernel's 20 roles)
-constexpr int BATCH_LANE_CTAS = 38;
+constexpr int BATCH_LANE_CTAS = 25;
 int sm_count() {
   static int sms[64] = {};
   int dev = 0;
