@@ -129,7 +129,12 @@ int ht_reduce_ex(int n, double* A, int lda, double* B, int ldb, double* Q, int l
  *   A, B, Q, Z    HOST arrays of `batch` device pointers (Q[i], Z[i] have
  *                 leading dimension n[i]; ignored when want_qz == 0)
  * Each pencil follows the rules of ht_reduce.  Pencils are independent; the
- * library orders them largest first.
+ * library reduces them largest first on concurrent lanes (host threads with
+ * streams of their own, ordered after the caller's earlier work on `stream`;
+ * `stream` waits for all of them), each launch whose CTAs wait on one another
+ * capped at a share of the SMs so that the lanes' launches are resident
+ * together.  Returns the first error of any pencil (the others may be
+ * incomplete then).  Blocks until every pencil is done.
  */
 int ht_reduce_batched(int batch, const int* n, double* const* A, const int* lda, double* const* B,
                       const int* ldb, double* const* Q, double* const* Z, int want_qz, ht_stream_t stream);
