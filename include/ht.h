@@ -126,8 +126,10 @@ int ht_reduce_ex(int n, double* A, int lda, double* B, int ldb, double* Q, int l
  * ht_reduce_batched -- HT reduction of `batch` independent pencils of
  * (possibly different) orders.
  *   n, lda, ldb   HOST arrays of length batch
- *   A, B, Q, Z    HOST arrays of `batch` device pointers (Q[i], Z[i] have
- *                 leading dimension n[i]; ignored when want_qz == 0)
+ *   A, B, Q, Z    arrays of `batch` device pointers, in host memory or in
+ *                 device memory (the cuBLAS-batched convention; a device
+ *                 array is copied to the host first); Q[i], Z[i] have
+ *                 leading dimension n[i] (ignored when want_qz == 0)
  * Each pencil follows the rules of ht_reduce.  Pencils are independent; the
  * library reduces them largest first on concurrent lanes (host threads with
  * streams of their own, ordered after the caller's earlier work on `stream`;

@@ -837,6 +837,26 @@ int ht_reduce_batched(int batch, const int* n, double* const* A, const int* lda,
   if (batch > 0 && (!n || !A || !lda || !B || !ldb)) return -2;
   if (want_qz && batch > 0 && (!Q || !Z)) return -7;
   if (batch == 0) return HT_OK;
+  // the pointer arrays may be host arrays or device arrays (the cuBLAS-batched
+  // convention): device arrays are copied to the host, which plans the lanes
+  std::vector<double*> hp[4];
+  double* const* parr[4] = {A, B, want_qz ? Q : nullptr, want_qz ? Z : nullptr};
+  for (int a = 0; a < 4; ++a) {
+    if (!parr[a]) continue;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, parr[a]) != cudaSuccess) {
+      cudaGetLastError();
+      continue;  // unregistered host memory
+    }
+    if (at.type == cudaMemoryTypeDevice) {
+      hp[a].resize(batch);
+      if (cudaMemcpy(hp[a].data(), parr[a], sizeof(double*) * (size_t)batch, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return HT_ERR_CUDA;
+      parr[a] = hp[a].data();
+    }
+  }
+  A = parr[0]; B = parr[1];
+  if (want_qz) { Q = parr[2]; Z = parr[3]; }
   std::vector<int> order(batch);
   for (int i = 0; i < batch; ++i) order[i] = i;
   std::sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });

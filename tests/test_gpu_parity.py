@@ -220,6 +220,35 @@ def test_batched_lanes_match_single_calls(ht):
             assert err <= 1e-10 * max(1.0, float(np.max(np.abs(a)))), (n, name, err)
 
 
+def test_batched_device_pointer_arrays(ht):
+    """ht_reduce_batched with its pointer arrays in device memory (the
+    cuBLAS-batched convention) gives the results of host pointer arrays."""
+    sizes = [150, 7, 90]
+    out = []
+    for dev_arrays in (False, True):
+        As, Bs, Qs, Zs = [], [], [], []
+        for i, n in enumerate(sizes):
+            A, B = pencils.random_qr(n, 2500 + i)
+            As.append(ht.colmajor(A)); Bs.append(ht.colmajor(B))
+            Qs.append(ht.colmajor(np.zeros((n, n)))); Zs.append(ht.colmajor(np.zeros((n, n))))
+        n_arr = (ctypes.c_int * 3)(*sizes)
+        ld = (ctypes.c_int * 3)(*sizes)
+        ptrs = [[x.data_ptr() for x in L] for L in (As, Bs, Qs, Zs)]
+        if dev_arrays:
+            keep = [torch.tensor(p, dtype=torch.int64, device="cuda") for p in ptrs]
+            args = [ctypes.cast(ctypes.c_void_p(t.data_ptr()), ctypes.POINTER(ctypes.c_void_p)) for t in keep]
+        else:
+            args = [(ctypes.c_void_p * 3)(*p) for p in ptrs]
+        torch.cuda.synchronize()
+        rc = ht.lib().ht_reduce_batched(3, n_arr, args[0], ld, args[1], ld, args[2], args[3], 1, None)
+        assert rc == 0
+        torch.cuda.synchronize()
+        out.append([[x.cpu().numpy() for x in L] for L in (As, Bs, Qs, Zs)])
+    for L0, L1 in zip(out[0], out[1]):
+        for a, b in zip(L0, L1):
+            assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "emu"])
 def test_elementwise_vs_algorithm1_three_solve_blocks(ht, prec):
     """n = 600: the trailing system has up to 599 rows, so the look-ahead
