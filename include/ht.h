@@ -69,7 +69,13 @@ typedef struct ht_options {
   int profile;         /* 1: time every launch by class into ht_stats (adds syncs) */
   int wait_polls;      /* test option: polls before a bounded device-side wait gives up and the call returns
                           HT_ERR_TIMEOUT; 0 = default (2^22 polls, seconds) */
-  int reserved[6];
+  int preprocess;      /* 1: deflate the zero columns of B first (Sec. 3.4.1): with l > 1 zero columns, a
+                          permutation Z_0 moves them to the front (Q_0 = Z_0 when B is diagonal, else I), a QR
+                          of the first l columns of Q_0^T A Z_0 makes them upper triangular (l infinite
+                          eigenvalues, already in generalized Schur form) and only the trailing pencil, after
+                          a QR of its B, is reduced; H and T keep the form of ht_reduce.  Allocates
+                          temporaries (about 3 n^2 doubles).  0: off */
+  int reserved[5];
 } ht_options;
 
 /* Launch classes of ht_stats.ms_by_class / flops_by_class / launches_by_class. */
@@ -121,6 +127,20 @@ int ht_reduce(int n, double* A, int lda, double* B, int ldb, double* Q, double* 
  * (NULL = defaults) and counters (NULL = not wanted). */
 int ht_reduce_ex(int n, double* A, int lda, double* B, int ldb, double* Q, int ldq, double* Z, int ldz,
                  int want_qz, const ht_options* opt, ht_stats* stats, ht_stream_t stream);
+
+/*
+ * ht_reduce_general -- the HT reduction of a pencil whose B is a general
+ * matrix: the front end of the QZ algorithm (Sec. 1) first computes the QR
+ * factorization B = Q_B R (Householder, DLARFG rule of Sec. 2.1), sets
+ * A <- Q_B^T A, B <- R, and then runs Algorithm 1 with Q starting from Q_B, so
+ * that H = Q^T A Z and T = Q^T B Z hold for the input A and B.
+ *   Arguments as ht_reduce_ex; B (device, n x n, ld ldb) need not be upper
+ *   triangular.  opt->preprocess is not available here (it needs an upper
+ *   triangular B) and returns HT_ERR_NOT_IMPLEMENTED.  Allocates a QR
+ *   workspace of about 34 n doubles for the call.
+ */
+int ht_reduce_general(int n, double* A, int lda, double* B, int ldb, double* Q, int ldq, double* Z, int ldz,
+                      int want_qz, const ht_options* opt, ht_stats* stats, ht_stream_t stream);
 
 /*
  * ht_reduce_batched -- HT reduction of `batch` independent pencils of

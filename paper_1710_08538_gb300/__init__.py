@@ -31,14 +31,15 @@ HT_NOALLOC_NMAX = 512
 HT_PREC_FP64 = 0
 HT_PREC_EMU = 1
 
-EXPORTED = ["ht_reduce", "ht_reduce_ex", "ht_reduce_batched", "ht_reduce_noalloc", "ht_last_device_status",
-            "ht_finalize", "ht_status_string", "ht_version", "ht_philox4x32_10"]
+EXPORTED = ["ht_reduce", "ht_reduce_ex", "ht_reduce_general", "ht_reduce_batched", "ht_reduce_noalloc",
+            "ht_last_device_status", "ht_finalize", "ht_status_string", "ht_version", "ht_philox4x32_10"]
 
 
 class HtOptions(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int), ("max_ir", ctypes.c_int), ("ir_tol_scale", ctypes.c_double),
                 ("precision", ctypes.c_int), ("emu_slices", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("profile", ctypes.c_int), ("wait_polls", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+                ("profile", ctypes.c_int), ("wait_polls", ctypes.c_int), ("preprocess", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class HtStats(ctypes.Structure):
@@ -81,6 +82,8 @@ def lib() -> ctypes.CDLL:
         L.ht_reduce_ex.argtypes = [ip, dp, ip, dp, ip, dp, ip, dp, ip, ip, ctypes.POINTER(HtOptions),
                                    ctypes.POINTER(HtStats), vp]
         L.ht_reduce_ex.restype = ctypes.c_int
+        L.ht_reduce_general.argtypes = L.ht_reduce_ex.argtypes
+        L.ht_reduce_general.restype = ctypes.c_int
         L.ht_reduce_batched.argtypes = [ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_void_p),
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_void_p),
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_void_p),
@@ -138,12 +141,14 @@ def _stream_ptr(stream) -> int:
 
 
 def options(nb: int = 0, max_ir: int = 0, ir_tol_scale: float = 0.0, precision: int = HT_PREC_FP64,
-            emu_slices: int = 0, seed: int = 0, profile: int = 0, wait_polls: int = 0) -> HtOptions:
+            emu_slices: int = 0, seed: int = 0, profile: int = 0, wait_polls: int = 0,
+            preprocess: int = 0) -> HtOptions:
     o = HtOptions()
     o.nb, o.max_ir, o.ir_tol_scale, o.precision, o.emu_slices, o.seed = nb, max_ir, ir_tol_scale, precision, \
         emu_slices, seed
     o.profile = profile
     o.wait_polls = wait_polls
+    o.preprocess = preprocess
     return o
 
 
@@ -159,6 +164,22 @@ def reduce(A, B, Q=None, Z=None, want_qz: bool = True, opts: HtOptions | None = 
     rc = lib().ht_reduce_ex(n, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), qp, ldq, zp, ldz, int(want_qz),
                             ctypes.byref(opts) if opts is not None else None,
                             ctypes.byref(st) if with_stats else None, _stream_ptr(stream))
+    _check(rc)
+    return st.as_dict() if with_stats else None
+
+
+def reduce_general(A, B, Q=None, Z=None, want_qz: bool = True, opts: HtOptions | None = None, stream=None,
+                   with_stats: bool = False):
+    """ht_reduce_general (B a general matrix: QR front end, then Algorithm 1) on torch tensors."""
+    n = A.shape[0]
+    st = HtStats()
+    qp = Q.data_ptr() if (want_qz and Q is not None) else None
+    zp = Z.data_ptr() if (want_qz and Z is not None) else None
+    ldq = _ld(Q) if (want_qz and Q is not None) else max(1, n)
+    ldz = _ld(Z) if (want_qz and Z is not None) else max(1, n)
+    rc = lib().ht_reduce_general(n, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), qp, ldq, zp, ldz, int(want_qz),
+                                 ctypes.byref(opts) if opts is not None else None,
+                                 ctypes.byref(st) if with_stats else None, _stream_ptr(stream))
     _check(rc)
     return st.as_dict() if with_stats else None
 

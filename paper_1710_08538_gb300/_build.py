@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libht.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
-SOURCES = ["ht_api.cu", "ht_panel.cu", "ht_factor.cu", "ht_apply.cu", "ht_noalloc.cu", "ht_tc.cu", "ht_chain.cu"]
+SOURCES = ["ht_api.cu", "ht_panel.cu", "ht_factor.cu", "ht_apply.cu", "ht_noalloc.cu", "ht_tc.cu", "ht_chain.cu", "ht_qr.cu"]
 
 
 def _nvcc() -> str:

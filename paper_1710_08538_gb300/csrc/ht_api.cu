@@ -633,8 +633,13 @@ int check_args(int n, const void* A, int lda, const void* B, int ldb, const void
   return HT_OK;
 }
 
+int preprocess_impl(int n, double* A, int lda, double* B, int ldb, double* Q, int ldq, double* Z, int ldz,
+                    int want_qz, const ht_options* opt, ht_stats* stats, cudaStream_t st, bool* done);
+
+// keep_q: Q already holds a left transform (a front end's) that the reduction
+// multiplies from the right, instead of starting from Q = I
 int reduce_impl(int n, double* A, int lda, double* B, int ldb, double* Q, int ldq, double* Z, int ldz, int want_qz,
-                const ht_options* opt, ht_stats* stats, cudaStream_t st, int cap = 0) {
+                const ht_options* opt, ht_stats* stats, cudaStream_t st, int cap = 0, bool keep_q = false) {
   int rc = check_args(n, A, lda, B, ldb, Q, ldq, Z, ldz, want_qz);
   if (rc != HT_OK) return rc;
   int nb = 32, max_ir = 10, prec = HT_PREC_FP64;
@@ -657,8 +662,13 @@ int reduce_impl(int n, double* A, int lda, double* B, int ldb, double* Q, int ld
   if (stats) std::memset(stats, 0, sizeof(*stats));
   set_stream_status(st, HT_OK);
   if (n == 0) return HT_OK;
+  if (opt && opt->preprocess && n > 2 && !keep_q) {
+    bool done = false;
+    rc = preprocess_impl(n, A, lda, B, ldb, Q, ldq, Z, ldz, want_qz, opt, stats, st, &done);
+    if (rc != HT_OK || done) return rc;
+  }
   if (want_qz) {
-    HT_CUDA(ht_launch_set_identity(st, Q, ldq, n));
+    if (!keep_q) HT_CUDA(ht_launch_set_identity(st, Q, ldq, n));
     HT_CUDA(ht_launch_set_identity(st, Z, ldz, n));
   }
   if (n <= 2) {
@@ -676,6 +686,112 @@ int reduce_impl(int n, double* A, int lda, double* B, int ldb, double* Q, int ld
                                     nb, max_ir, tol_scale, seed, opt && opt->profile, stats, st);
   release(pe);
   return result;
+}
+
+// Device memory of the front ends (freed on scope exit, after the stream's work)
+struct DevBuf {
+  void* p = nullptr;
+  cudaStream_t st = nullptr;
+  ~DevBuf() {
+    if (p) {
+      cudaStreamSynchronize(st);
+      cudaFree(p);
+    }
+  }
+  bool alloc(size_t bytes, cudaStream_t s) {
+    st = s;
+    return cudaMalloc(&p, bytes > 0 ? bytes : 1) == cudaSuccess;
+  }
+  double* d() const { return (double*)p; }
+};
+
+// QZ front end (Sec. 1): B = Q_B R, A <- Q_B^T A, Q <- Q_B (when want_qz), B <- R
+int front_end_qr(int n, double* A, int lda, double* B, int ldb, double* Q, int ldq, int want_qz, cudaStream_t st) {
+  if (n <= 0) return HT_OK;
+  DevBuf ws;
+  if (!ws.alloc(ht_qr_ws_doubles(n, n, n) * sizeof(double), st)) return HT_ERR_NOMEM;
+  if (want_qz) HT_CUDA(ht_launch_set_identity(st, Q, ldq, n));
+  const HtQrTarget tg = {A, lda, n};
+  HT_CUDA(ht_qr_blocked(st, n, n, B, ldb, &tg, 1, want_qz ? Q : nullptr, ldq, n, ws.d()));
+  return HT_OK;
+}
+
+// Sec. 3.4.1 (see ht_options.preprocess).  *done = false: nothing to deflate
+// (at most one zero column), the caller reduces the pencil as it is.
+int preprocess_impl(int n, double* A, int lda, double* B, int ldb, double* Q, int ldq, double* Z, int ldz,
+                    int want_qz, const ht_options* opt, ht_stats* stats, cudaStream_t st, bool* done) {
+  *done = false;
+  DevBuf flags;
+  if (!flags.alloc((size_t)(n + 1) * sizeof(int), st)) return HT_ERR_NOMEM;
+  int* dz = (int*)flags.p;
+  HT_CUDA(ht_launch_zero_columns(st, n, B, ldb, dz, dz + n));
+  std::vector<int> hz(n + 1);
+  HT_CUDA(cudaMemcpyAsync(hz.data(), dz, (size_t)(n + 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
+  HT_CUDA(cudaStreamSynchronize(st));
+  std::vector<int> perm;
+  for (int c = 0; c < n; ++c)
+    if (hz[c]) perm.push_back(c);
+  const int l = (int)perm.size();
+  if (l <= 1) return HT_OK;
+  for (int c = 0; c < n; ++c)
+    if (!hz[c]) perm.push_back(c);
+  const bool diag = hz[n] == 0;  // B diagonal: Q_0 = Z_0 keeps it so
+  *done = true;
+  const int m2 = n - l;
+  const size_t nn = (size_t)n * n, mm = (size_t)m2 * m2;
+  DevBuf mem;
+  const size_t ws_d = ht_qr_ws_doubles(n, n, n);
+  if (!mem.alloc((nn + 2 * mm + ws_d) * sizeof(double) + (size_t)n * sizeof(int), st)) return HT_ERR_NOMEM;
+  double* tmp = mem.d();
+  double* Q22 = tmp + nn;
+  double* Z22 = Q22 + mm;
+  double* ws = Z22 + mm;
+  int* dp = (int*)(ws + ws_d);
+  HT_CUDA(cudaMemcpyAsync(dp, perm.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, st));
+  // A_0 = Q_0^T A Z_0, B_0 = Q_0^T B Z_0; Q = Q_0, Z = Z_0
+  HT_CUDA(ht_launch_permute(st, n, A, lda, tmp, dp, diag ? 1 : 0));
+  HT_CUDA(ht_launch_permute(st, n, B, ldb, tmp, dp, diag ? 1 : 0));
+  if (want_qz) {
+    if (diag) HT_CUDA(ht_launch_perm_matrix(st, n, Q, ldq, dp));
+    else HT_CUDA(ht_launch_set_identity(st, Q, ldq, n));
+    HT_CUDA(ht_launch_perm_matrix(st, n, Z, ldz, dp));
+  }
+  // QR of the first l columns of A_0: A_1 = [A11 A12; 0 A22], B_1 = [0 B12; 0 B22]
+  const HtQrTarget tg[2] = {{A + (size_t)l * lda, lda, m2}, {B, ldb, n}};
+  HT_CUDA(ht_qr_blocked(st, n, l, A, lda, tg, 2, want_qz ? Q : nullptr, ldq, n, ws));
+  if (m2 == 0) {
+    set_stream_status(st, HT_OK);
+    HT_CUDA(cudaStreamSynchronize(st));
+    return HT_OK;
+  }
+  // the trailing pencil: QR of B22 (front end), then Algorithm 1 with Q22, Z22
+  double* A22 = A + (size_t)l + (size_t)l * lda;
+  double* B22 = B + (size_t)l + (size_t)l * ldb;
+  HT_CUDA(ht_launch_set_identity(st, Q22, m2, m2));
+  {
+    const HtQrTarget t22 = {A22, lda, m2};
+    HT_CUDA(ht_qr_blocked(st, m2, m2, B22, ldb, &t22, 1, Q22, m2, m2, ws));
+  }
+  ht_options o2 = *opt;
+  o2.preprocess = 0;
+  const int rc = reduce_impl(m2, A22, lda, B22, ldb, Q22, m2, Z22, m2, 1, &o2, stats, st, 0, true);
+  if (rc != HT_OK) return rc;
+  // rows 0 .. l-1 of A and B take Z22 from the right; Q and Z their trailing columns
+  auto right_mul = [&](double* X, long ldx, int rows, const double* M) -> cudaError_t {
+    if (rows <= 0) return cudaSuccess;
+    cudaError_t e = ht_gemm(st, 'N', 'N', rows, m2, m2, 1.0, X, (int)ldx, M, m2, 0.0, tmp, rows);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy2DAsync(X, ldx * sizeof(double), tmp, rows * sizeof(double), rows * sizeof(double), m2,
+                             cudaMemcpyDeviceToDevice, st);
+  };
+  HT_CUDA(right_mul(A + (size_t)l * lda, lda, l, Z22));
+  HT_CUDA(right_mul(B + (size_t)l * ldb, ldb, l, Z22));
+  if (want_qz) {
+    HT_CUDA(right_mul(Q + (size_t)l * ldq, ldq, n, Q22));
+    HT_CUDA(right_mul(Z + (size_t)l * ldz, ldz, n, Z22));
+  }
+  HT_CUDA(cudaStreamSynchronize(st));
+  return HT_OK;
 }
 
 }  // namespace
@@ -825,6 +941,17 @@ extern "C" {
 int ht_reduce_ex(int n, double* A, int lda, double* B, int ldb, double* Q, int ldq, double* Z, int ldz, int want_qz,
                  const ht_options* opt, ht_stats* stats, ht_stream_t stream) {
   return reduce_impl(n, A, lda, B, ldb, Q, ldq, Z, ldz, want_qz, opt, stats, (cudaStream_t)stream);
+}
+
+int ht_reduce_general(int n, double* A, int lda, double* B, int ldb, double* Q, int ldq, double* Z, int ldz,
+                      int want_qz, const ht_options* opt, ht_stats* stats, ht_stream_t stream) {
+  int rc = check_args(n, A, lda, B, ldb, Q, ldq, Z, ldz, want_qz);
+  if (rc != HT_OK) return rc;
+  if (opt && opt->preprocess) return HT_ERR_NOT_IMPLEMENTED;  // preprocessing needs an upper triangular B
+  cudaStream_t st = (cudaStream_t)stream;
+  rc = front_end_qr(n, A, lda, B, ldb, Q, ldq, want_qz, st);
+  if (rc != HT_OK) return rc;
+  return reduce_impl(n, A, lda, B, ldb, Q, ldq, Z, ldz, want_qz, opt, stats, st, 0, true);
 }
 
 int ht_reduce(int n, double* A, int lda, double* B, int ldb, double* Q, double* Z, int want_qz, ht_stream_t stream) {

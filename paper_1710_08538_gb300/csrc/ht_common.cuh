@@ -240,6 +240,26 @@ cudaError_t ht_launch_zero(cudaStream_t st, double* X, long ldx, int rows, int c
 cudaError_t ht_launch_set_identity(cudaStream_t st, double* X, long ldx, int n);
 cudaError_t ht_launch_check_finite(cudaStream_t st, const double* X, long ldx, int n, int upper_only, int* err);
 
+// Dense Householder QR (ht_qr.cu): M (m x nc) <- R in place (exact zeros below),
+// the same reflectors applied from the left to every target (its rows aligned
+// with M's) and from the right to Qm (nq rows): Qm <- Qm Q_M.  ws: at least
+// ht_qr_ws_doubles(m, max(nc, targets' columns), nq) doubles.
+struct HtQrTarget {
+  double* X;
+  long ld;
+  int ncols;
+};
+size_t ht_qr_ws_doubles(int m, int nx, int nq);
+cudaError_t ht_qr_blocked(cudaStream_t st, int m, int nc, double* M, long ldm, const HtQrTarget* left, int nleft,
+                          double* Qm, long ldq, int nq, double* ws);
+// zc[c] = 1 when column c of the upper triangle of B is zero; *offdiag = 1 when
+// B has a nonzero above its diagonal
+cudaError_t ht_launch_zero_columns(cudaStream_t st, int n, const double* B, long ldb, int* zc, int* offdiag);
+// X <- X(:, p) (and rows X(p, :) when rows != 0) through tmp (n x n, ld n); p on the device
+cudaError_t ht_launch_permute(cudaStream_t st, int n, double* X, long ldx, double* tmp, const int* p, int rows);
+// X <- the permutation matrix with X(p[i], i) = 1
+cudaError_t ht_launch_perm_matrix(cudaStream_t st, int n, double* X, long ldx, const int* p);
+
 // WY store helpers
 __host__ __device__ inline size_t ht_wy_half(size_t stride) { return stride / 2; }
 
