@@ -42,7 +42,8 @@ void set_stream_status(cudaStream_t st, int v) {
 // Workspace pool (keyed by device, order and panel width)
 // ---------------------------------------------------------------------------
 struct PoolEntry {
-  int dev, n, nb;
+  int dev, n, nb;             // n: the order the buffer was sized for
+  int cur_n;                  // the order its workspace is laid out for now (<= n)
   int G;                      // CTAs of the cooperative panel on the whole GPU
   bool busy;
   HtWork w;
@@ -172,6 +173,7 @@ int alloc_work(PoolEntry* e, int n, int nb) {
   ht_layout_work(w, (char*)base, n, nb, G, &e->pt_dev, true);
   e->base = base;
   e->G = G;
+  e->cur_n = n;
   // the side stream of the Q / Z updates and its events (without them, one stream)
   if (cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking) != cudaSuccess) {
     w.side = nullptr;
@@ -191,16 +193,40 @@ int alloc_work(PoolEntry* e, int n, int nb) {
   return HT_OK;
 }
 
+// A free workspace laid out for order n, or else the smallest free one sized
+// for an order in [n, 2n] (laid out again for n, cleared: its epoch-stamped
+// progress words start over), or else a new one.
 PoolEntry* acquire(int n, int nb, int* rc) {
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(g_pool_mu);
   for (PoolEntry* e : g_pool)
-    if (!e->busy && e->dev == dev && e->n == n && e->nb == nb) {
+    if (!e->busy && e->dev == dev && e->cur_n == n && e->nb == nb) {
       e->busy = true;
       *rc = HT_OK;
       return e;
     }
+  PoolEntry* best = nullptr;
+  for (PoolEntry* e : g_pool)
+    if (!e->busy && e->dev == dev && e->nb == nb && e->n >= n && e->n <= 2 * n && (!best || e->n < best->n)) best = e;
+  if (best) {
+    HtWork& w = best->w;
+    const cudaStream_t side = w.side;
+    cudaEvent_t ev[5];
+    for (int i = 0; i < 5; ++i) ev[i] = w.side_ev[i];
+    best->cur_n = -1;  // until the clear below succeeds
+    const size_t bytes = ht_layout_work(w, (char*)best->base, n, nb, best->G, &best->pt_dev, true);
+    w.side = side;
+    for (int i = 0; i < 5; ++i) w.side_ev[i] = ev[i];
+    if (cudaMemset(best->base, 0, bytes) != cudaSuccess) {
+      *rc = HT_ERR_CUDA;
+      return nullptr;
+    }
+    best->cur_n = n;
+    best->busy = true;
+    *rc = HT_OK;
+    return best;
+  }
   PoolEntry* e = new PoolEntry();
   e->dev = dev; e->n = n; e->nb = nb; e->busy = true;
   *rc = alloc_work(e, n, nb);
