@@ -75,7 +75,14 @@ typedef struct ht_options {
                           eigenvalues, already in generalized Schur form) and only the trailing pencil, after
                           a QR of its B, is reduced; H and T keep the form of ht_reduce.  Allocates
                           temporaries (about 3 n^2 doubles).  0: off */
-  int reserved[5];
+  int emu_check;       /* HT_PREC_EMU with want_qz: 1 = after the reduction, estimate the relative backward
+                          errors ||Q H Z^T - A||_F / ||A||_F and ||Q T Z^T - B||_F / ||B||_F with 8 Gaussian
+                          probes and FP64 products, report them in ht_stats.emu_bwd_est and, when one exceeds
+                          1e-12 (the stated accuracy of the emulated path), redo the reduction with
+                          HT_PREC_FP64 from a saved copy of A and B (ht_stats.emu_fallback = 1); allocates
+                          2 n^2 + 32 n doubles.  2 = the same with the check treated as failed (a test of the
+                          fallback).  0: off */
+  int reserved[4];
 } ht_options;
 
 /* Launch classes of ht_stats.ms_by_class / flops_by_class / launches_by_class. */
@@ -106,6 +113,8 @@ typedef struct ht_stats {
   double flops_by_class[HT_NCLASS];     /* algorithmic flops per launch class */
   long long launches_by_class[HT_NCLASS];
   double panel_phase_ms[24];            /* panel (0-15) and restore (16-19) time by phase (profile = 1) */
+  double emu_bwd_est[2];   /* ht_options.emu_check: probe estimates of the backward errors of A and B */
+  int emu_fallback;        /* ht_options.emu_check: 1 when the reduction was redone in FP64 */
 } ht_stats;
 
 /*

@@ -39,7 +39,7 @@ class HtOptions(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int), ("max_ir", ctypes.c_int), ("ir_tol_scale", ctypes.c_double),
                 ("precision", ctypes.c_int), ("emu_slices", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("profile", ctypes.c_int), ("wait_polls", ctypes.c_int), ("preprocess", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("emu_check", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class HtStats(ctypes.Structure):
@@ -47,7 +47,8 @@ class HtStats(ctypes.Structure):
                 ("cols_with_ir", ctypes.c_longlong), ("perturbed_pivots", ctypes.c_int),
                 ("ms_panel", ctypes.c_double), ("ms_absorb", ctypes.c_double), ("flops_nominal", ctypes.c_double),
                 ("ms_by_class", ctypes.c_double * 8), ("flops_by_class", ctypes.c_double * 8),
-                ("launches_by_class", ctypes.c_longlong * 8), ("panel_phase_ms", ctypes.c_double * 24)]
+                ("launches_by_class", ctypes.c_longlong * 8), ("panel_phase_ms", ctypes.c_double * 24),
+                ("emu_bwd_est", ctypes.c_double * 2), ("emu_fallback", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         out = {}
@@ -142,13 +143,14 @@ def _stream_ptr(stream) -> int:
 
 def options(nb: int = 0, max_ir: int = 0, ir_tol_scale: float = 0.0, precision: int = HT_PREC_FP64,
             emu_slices: int = 0, seed: int = 0, profile: int = 0, wait_polls: int = 0,
-            preprocess: int = 0) -> HtOptions:
+            preprocess: int = 0, emu_check: int = 0) -> HtOptions:
     o = HtOptions()
     o.nb, o.max_ir, o.ir_tol_scale, o.precision, o.emu_slices, o.seed = nb, max_ir, ir_tol_scale, precision, \
         emu_slices, seed
     o.profile = profile
     o.wait_polls = wait_polls
     o.preprocess = preprocess
+    o.emu_check = emu_check
     return o
 
 

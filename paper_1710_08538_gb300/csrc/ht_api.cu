@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -661,6 +662,8 @@ int check_args(int n, const void* A, int lda, const void* B, int ldb, const void
 
 int preprocess_impl(int n, double* A, int lda, double* B, int ldb, double* Q, int ldq, double* Z, int ldz,
                     int want_qz, const ht_options* opt, ht_stats* stats, cudaStream_t st, bool* done);
+int checked_emu(int n, double* A, int lda, double* B, int ldb, double* Q, int ldq, double* Z, int ldz,
+                const ht_options* opt, ht_stats* stats, cudaStream_t st);
 
 // keep_q: Q already holds a left transform (a front end's) that the reduction
 // multiplies from the right, instead of starting from Q = I
@@ -688,6 +691,8 @@ int reduce_impl(int n, double* A, int lda, double* B, int ldb, double* Q, int ld
   if (stats) std::memset(stats, 0, sizeof(*stats));
   set_stream_status(st, HT_OK);
   if (n == 0) return HT_OK;
+  if (opt && opt->emu_check && prec == HT_PREC_EMU && want_qz && n > 2 && !keep_q && !opt->preprocess)
+    return checked_emu(n, A, lda, B, ldb, Q, ldq, Z, ldz, opt, stats, st);
   if (opt && opt->preprocess && n > 2 && !keep_q) {
     bool done = false;
     rc = preprocess_impl(n, A, lda, B, ldb, Q, ldq, Z, ldz, want_qz, opt, stats, st, &done);
@@ -739,6 +744,66 @@ int front_end_qr(int n, double* A, int lda, double* B, int ldb, double* Q, int l
   if (want_qz) HT_CUDA(ht_launch_set_identity(st, Q, ldq, n));
   const HtQrTarget tg = {A, lda, n};
   HT_CUDA(ht_qr_blocked(st, n, n, B, ldb, &tg, 1, want_qz ? Q : nullptr, ldq, n, ws.d()));
+  return HT_OK;
+}
+
+// ht_options.emu_check: the emulated reduction, a probe estimate of its
+// backward errors with FP64 products, and a rerun in FP64 from a saved copy of
+// the pencil when an estimate exceeds the emulated path's stated 1e-12.
+int checked_emu(int n, double* A, int lda, double* B, int ldb, double* Q, int ldq, double* Z, int ldz,
+                const ht_options* opt, ht_stats* stats, cudaStream_t st) {
+  constexpr int NP = 8;
+  const size_t nn = (size_t)n * n;
+  DevBuf mem;
+  if (!mem.alloc((2 * nn + 4 * (size_t)n * NP + 8) * sizeof(double), st)) return HT_ERR_NOMEM;
+  double* A0 = mem.d();
+  double* B0 = A0 + nn;
+  double* X = B0 + nn;
+  double* Y1 = X + (size_t)n * NP;
+  double* Y2 = Y1 + (size_t)n * NP;
+  double* Y3 = Y2 + (size_t)n * NP;
+  double* acc = Y3 + (size_t)n * NP;  // |A|^2, |B|^2, |dA X|^2, |dB X|^2
+  const size_t row = (size_t)n * sizeof(double);
+  HT_CUDA(cudaMemcpy2DAsync(A0, row, A, lda * sizeof(double), row, n, cudaMemcpyDeviceToDevice, st));
+  HT_CUDA(cudaMemcpy2DAsync(B0, row, B, ldb * sizeof(double), row, n, cudaMemcpyDeviceToDevice, st));
+  HT_CUDA(ht_launch_zero(st, B0, n, n, n, 1));  // B is upper triangular: its strictly lower part is ignored
+  ht_options o2 = *opt;
+  o2.emu_check = 0;
+  int rc = reduce_impl(n, A, lda, B, ldb, Q, ldq, Z, ldz, 1, &o2, stats, st);
+  if (rc != HT_OK) return rc;
+  // ||Q M Z^T X - M0 X||_F over 8 probes estimates ||Q M Z^T - M0||_F sqrt(8)
+  HT_CUDA(cudaMemsetAsync(acc, 0, 8 * sizeof(double), st));
+  HT_CUDA(ht_launch_sumsq(st, n, n, A0, n, nullptr, 0, acc + 0));
+  HT_CUDA(ht_launch_sumsq(st, n, n, B0, n, nullptr, 0, acc + 1));
+  HT_CUDA(ht_launch_gauss(st, (size_t)n * NP, X, 0x5EEDull + (unsigned long long)n));
+  const double* M[2] = {A, B};
+  const int ldm[2] = {lda, ldb};
+  const double* M0[2] = {A0, B0};
+  for (int t = 0; t < 2; ++t) {
+    HT_CUDA(ht_gemm(st, 'T', 'N', n, NP, n, 1.0, Z, ldz, X, n, 0.0, Y1, n));
+    HT_CUDA(ht_gemm(st, 'N', 'N', n, NP, n, 1.0, M[t], ldm[t], Y1, n, 0.0, Y2, n));
+    HT_CUDA(ht_gemm(st, 'N', 'N', n, NP, n, 1.0, Q, ldq, Y2, n, 0.0, Y3, n));
+    HT_CUDA(ht_gemm(st, 'N', 'N', n, NP, n, 1.0, M0[t], n, X, n, 0.0, Y1, n));
+    HT_CUDA(ht_launch_sumsq(st, n, NP, Y3, n, Y1, n, acc + 2 + t));
+  }
+  double h[4] = {0, 0, 0, 0};
+  HT_CUDA(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, st));
+  HT_CUDA(cudaStreamSynchronize(st));
+  const double ea = h[0] > 0 ? std::sqrt(h[2] / NP / h[0]) : 0.0;
+  const double eb = h[1] > 0 ? std::sqrt(h[3] / NP / h[1]) : 0.0;
+  const bool fail = !(ea <= 1e-12 && eb <= 1e-12) || opt->emu_check == 2;
+  if (fail) {
+    HT_CUDA(cudaMemcpy2DAsync(A, lda * sizeof(double), A0, row, row, n, cudaMemcpyDeviceToDevice, st));
+    HT_CUDA(cudaMemcpy2DAsync(B, ldb * sizeof(double), B0, row, row, n, cudaMemcpyDeviceToDevice, st));
+    o2.precision = HT_PREC_FP64;
+    rc = reduce_impl(n, A, lda, B, ldb, Q, ldq, Z, ldz, 1, &o2, stats, st);
+    if (rc != HT_OK) return rc;
+  }
+  if (stats) {
+    stats->emu_bwd_est[0] = ea;
+    stats->emu_bwd_est[1] = eb;
+    stats->emu_fallback = fail ? 1 : 0;
+  }
   return HT_OK;
 }
 

@@ -257,6 +257,11 @@ cudaError_t ht_qr_blocked(cudaStream_t st, int m, int nc, double* M, long ldm, c
 cudaError_t ht_launch_zero_columns(cudaStream_t st, int n, const double* B, long ldb, int* zc, int* offdiag);
 // X <- X(:, p) (and rows X(p, :) when rows != 0) through tmp (n x n, ld n); p on the device
 cudaError_t ht_launch_permute(cudaStream_t st, int n, double* X, long ldx, double* tmp, const int* p, int rows);
+// N(0,1) probe samples (count doubles) and a sum of squares of X - Y (Y null:
+// of X) over an m x c block added to *acc (ht_qr.cu)
+cudaError_t ht_launch_gauss(cudaStream_t st, size_t count, double* X, unsigned long long seed);
+cudaError_t ht_launch_sumsq(cudaStream_t st, int m, int c, const double* X, long ldx, const double* Y, long ldy,
+                            double* acc);
 // X <- the permutation matrix with X(p[i], i) = 1
 cudaError_t ht_launch_perm_matrix(cudaStream_t st, int n, double* X, long ldx, const int* p);
 

@@ -147,7 +147,56 @@ __global__ void perm_matrix_kernel(int n, double* X, long ldx, const int* p) {
   X[r + (size_t)i * ldx] = (r == p[i]) ? 1.0 : 0.0;
 }
 
+// ---- a-posteriori check of a reduction by Gaussian probes ----
+// X (n x np): N(0,1) samples from a counter hash (SplitMix64) and Box-Muller;
+// the probes only need to be independent of the data
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+__global__ void gauss_kernel(size_t count, double* X, unsigned long long seed) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= count) return;
+  const unsigned long long a = splitmix64(seed ^ (2 * e)), b = splitmix64(seed ^ (2 * e + 1));
+  const double u1 = ((a >> 11) + 1) * 0x1.0p-53, u2 = (b >> 11) * 0x1.0p-53;
+  X[e] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+}
+// acc[slot] += sum over the m x c block (ld) of (X - Y)^2 (Y null: X^2)
+__global__ void sumsq_kernel(int m, int c, const double* X, long ldx, const double* Y, long ldy, double* acc) {
+  __shared__ double red[8];
+  double s = 0.0;
+  const size_t tot = (size_t)m * c;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = e % m, j = e / m;
+    const double d = X[r + j * ldx] - (Y ? Y[r + j * ldy] : 0.0);
+    s += d * d;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    atomicAdd(acc, t);
+  }
+}
+
 }  // namespace
+
+cudaError_t ht_launch_gauss(cudaStream_t st, size_t count, double* X, unsigned long long seed) {
+  if (count == 0) return cudaSuccess;
+  gauss_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(count, X, seed);
+  return cudaGetLastError();
+}
+
+cudaError_t ht_launch_sumsq(cudaStream_t st, int m, int c, const double* X, long ldx, const double* Y, long ldy,
+                            double* acc) {
+  if (m <= 0 || c <= 0) return cudaSuccess;
+  sumsq_kernel<<<304, 256, 0, st>>>(m, c, X, ldx, Y, ldy, acc);
+  return cudaGetLastError();
+}
 
 size_t ht_qr_ws_doubles(int m, int nx, int nq) {
   const size_t w = (size_t)std::max(nx, 1);

@@ -80,3 +80,27 @@ def test_last_device_status_is_per_stream(htlib):
     assert htlib.lib().ht_last_device_status(ctypes.c_void_p(0x7777), ctypes.byref(st)) == htlib.HT_OK
     assert st.value == htlib.HT_OK
     assert htlib.lib().ht_last_device_status(None, None) == -2
+
+
+def test_struct_layouts_match_the_header(htlib, tmp_path):
+    """The Python binding's ht_options and ht_stats have the sizes and field
+    offsets of the C declarations in include/ht.h (compiled here with gcc)."""
+    import ctypes
+    import subprocess
+    src = tmp_path / "sz.c"
+    fields_o = ["nb", "max_ir", "ir_tol_scale", "precision", "emu_slices", "seed", "profile", "wait_polls",
+                "preprocess", "emu_check"]
+    fields_s = ["panels", "ir_steps", "ms_panel", "flops_nominal", "ms_by_class", "launches_by_class",
+                "panel_phase_ms", "emu_bwd_est", "emu_fallback"]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ht.h"', "int main(void) {",
+             '  printf("%zu %zu\\n", sizeof(ht_options), sizeof(ht_stats));']
+    lines += [f'  printf("%zu\\n", offsetof(ht_options, {f}));' for f in fields_o]
+    lines += [f'  printf("%zu\\n", offsetof(ht_stats, {f}));' for f in fields_s]
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(htlib.HtOptions) and out[1] == ctypes.sizeof(htlib.HtStats)
+    got = [getattr(htlib.HtOptions, f).offset for f in fields_o] + [getattr(htlib.HtStats, f).offset for f in fields_s]
+    assert out[2:] == got

@@ -117,3 +117,34 @@ def test_emu_unsupported_options(ht):
     with pytest.raises(ht.HtError) as e:
         run(ht, A, B, nb=16, emu_slices=5)
     assert e.value.code == ht.HT_ERR_NOT_IMPLEMENTED
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_emu_check_and_fallback(ht, mode):
+    """ht_options.emu_check: mode 1 reports probe estimates of the backward
+    errors and keeps the emulated result when they hold the stated 1e-12;
+    mode 2 treats the check as failed and redoes the reduction in FP64 from
+    the saved pencil, which then equals an FP64 call bit for bit."""
+    n = 300
+    A, B = pencils.random_qr(n, 4300)
+    dA, dB = ht.colmajor(A), ht.colmajor(B)
+    dQ, dZ = ht.colmajor(np.zeros((n, n))), ht.colmajor(np.zeros((n, n)))
+    st = ht.reduce(dA, dB, dQ, dZ, opts=ht.options(precision=ht.HT_PREC_EMU, emu_check=mode), with_stats=True)
+    torch.cuda.synchronize()
+    got = [x.cpu().numpy() for x in (dA, dB, dQ, dZ)]
+    checks.assert_invariants(A, B, *got, bwd_tol=1e-12)
+    ea, eb = st["emu_bwd_est"]
+    rep = checks.invariant_report(A, B, *got)
+    assert 0.0 < ea <= 1e-12 and 0.0 < eb <= 1e-12, (ea, eb)
+    # the probe estimate is within a small factor of the true Frobenius-norm error
+    assert ea <= 5 * rep["bwd_a"] + 1e-16 and rep["bwd_a"] <= 5 * ea + 1e-16, (ea, rep["bwd_a"])
+    if mode == 1:
+        assert st["emu_fallback"] == 0
+    else:
+        assert st["emu_fallback"] == 1
+        fA, fB = ht.colmajor(A), ht.colmajor(B)
+        fQ, fZ = ht.colmajor(np.zeros((n, n))), ht.colmajor(np.zeros((n, n)))
+        ht.reduce(fA, fB, fQ, fZ, opts=ht.options(precision=ht.HT_PREC_FP64))
+        torch.cuda.synchronize()
+        for a, b in zip((fA, fB, fQ, fZ), got):
+            assert np.array_equal(a.cpu().numpy(), b)
