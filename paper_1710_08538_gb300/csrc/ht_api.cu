@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "ht_common.cuh"
+#include "ht_tuned.h"
 
 namespace {
 
@@ -1079,9 +1080,12 @@ int ht_reduce_batched(int batch, const int* n, double* const* A, const int* lda,
   for (int i = 0; i < batch; ++i) order[i] = i;
   std::sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
   cudaStream_t user = (cudaStream_t)stream;
+  // the panel width of each pencil's size class (ht_tuned.h, measured by the autotuner)
   auto one = [&](int i, cudaStream_t st, int cap) {
+    ht_options o{};
+    o.nb = ht_tuned_nb(n[i]);
     return reduce_impl(n[i], A[i], lda[i], B[i], ldb[i], want_qz ? Q[i] : nullptr, std::max(1, n[i]),
-                       want_qz ? Z[i] : nullptr, std::max(1, n[i]), want_qz, nullptr, nullptr, st, cap);
+                       want_qz ? Z[i] : nullptr, std::max(1, n[i]), want_qz, &o, nullptr, st, cap);
   };
   // Lanes: the pencils are independent, and one reduction of a small pencil
   // leaves most of the GPU idle (its panels and restore chains are latency-
