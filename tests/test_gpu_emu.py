@@ -97,6 +97,23 @@ def test_emu_config5_graded_n1024(ht):
     assert check.passes(rep, bwd_tol=EMU_BWD), rep
 
 
+def test_emu_config5_graded_full_size(ht):
+    """Config 5 at its own size: the graded pencil of order 8192 on the
+    emulated path, with the a-posteriori check on (probe estimates within the
+    stated 1e-12, no fallback) and 16-probe invariants in FP64 on the GPU."""
+    from paper_1710_08538_gb300 import check
+    n = 8192
+    A, B = pencils.graded(n, 8192)
+    dA, dB = ht.colmajor(A), ht.colmajor(B)
+    del A, B
+    A0, B0 = dA.clone(), dB.clone()
+    dQ, dZ = torch.empty_like(dA), torch.empty_like(dA)
+    st = ht.reduce(dA, dB, dQ, dZ, opts=ht.options(nb=32, precision=ht.HT_PREC_EMU, emu_check=1), with_stats=True)
+    assert st["emu_fallback"] == 0 and max(st["emu_bwd_est"]) <= EMU_BWD, st["emu_bwd_est"]
+    rep = check.invariants(A0, B0, dA, dB, dQ, dZ, probes=16, seed=3)
+    assert check.passes(rep, bwd_tol=EMU_BWD), rep
+
+
 def test_emu_config3_shape_n2048(ht):
     from paper_1710_08538_gb300 import check
     n = 2048
