@@ -165,7 +165,8 @@ int ht_reduce_general(int n, double* A, int lda, double* B, int ldb, double* Q, 
  * `stream` waits for all of them), each launch whose CTAs wait on one another
  * capped at a share of the SMs so that the lanes' launches are resident
  * together.  Returns the first error of any pencil (the others may be
- * incomplete then).  Blocks until every pencil is done.
+ * incomplete then); ht_last_device_status(stream) then reports it when it is
+ * a device-side condition.  Blocks until every pencil is done.
  */
 int ht_reduce_batched(int batch, const int* n, double* const* A, const int* lda, double* const* B,
                       const int* ldb, double* const* Q, double* const* Z, int want_qz, ht_stream_t stream);

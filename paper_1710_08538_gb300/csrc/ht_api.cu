@@ -1138,6 +1138,8 @@ int ht_reduce_batched(int batch, const int* n, double* const* A, const int* lda,
   }
   for (auto s2 : ls) if (s2) cudaStreamDestroy(s2);
   for (auto e2 : le) if (e2) cudaEventDestroy(e2);
+  // the caller's stream reports the batch: the first device-side error of any pencil
+  set_stream_status(user, (rc == HT_ERR_TIMEOUT || rc == HT_ERR_NONFINITE || rc == HT_ERR_INTERNAL) ? rc : HT_OK);
   return rc;
 }
 
