@@ -1119,16 +1119,25 @@ int ht_reduce_batched(int batch, const int* n, double* const* A, const int* lda,
   if (rc == HT_OK) {
     std::atomic<int> next{0}, err{HT_OK};
     std::vector<std::thread> th;
-    for (int l = 0; l < lanes; ++l)
-      th.emplace_back([&, l]() {
-        if (cudaSetDevice(dev) != cudaSuccess) { int z = HT_OK; err.compare_exchange_strong(z, HT_ERR_CUDA); return; }
-        for (;;) {
-          const int q = next.fetch_add(1);
-          if (q >= batch || err.load() != HT_OK) return;
-          const int r = one(order[q], ls[l], cap);
-          if (r != HT_OK) { int z = HT_OK; err.compare_exchange_strong(z, r); return; }
-        }
-      });
+    auto lane = [&](int l) {
+      if (cudaSetDevice(dev) != cudaSuccess) { int z = HT_OK; err.compare_exchange_strong(z, HT_ERR_CUDA); return; }
+      for (;;) {
+        const int q = next.fetch_add(1);
+        if (q >= batch || err.load() != HT_OK) return;
+        const int r = one(order[q], ls[l], cap);
+        if (r != HT_OK) { int z = HT_OK; err.compare_exchange_strong(z, r); return; }
+      }
+    };
+    // a lane whose thread cannot be started runs in this thread after the others start
+    std::vector<int> inline_lanes;
+    for (int l = 0; l < lanes; ++l) {
+      try {
+        th.emplace_back(lane, l);
+      } catch (...) {
+        inline_lanes.push_back(l);
+      }
+    }
+    for (int l : inline_lanes) lane(l);
     for (auto& t : th) t.join();
     rc = err.load();
     // the caller's stream follows every lane
