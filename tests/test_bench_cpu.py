@@ -76,3 +76,16 @@ def test_reference_arm_other_ranks_print_nothing():
     r = _reference_arm({"RANK": "1"})
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+@pytest.mark.parametrize("t_step,expect", [(40.0, (5, 20)), (66.0, (4, 20)), (72.0, (3, 19)), (400.0, (3, 1))])
+def test_plan_steps_fits_the_budget(t_step, expect):
+    """The wall-clock plan: the requested steps when they fit; else the
+    warm-up shrinks to 3 (never below), then the timed steps (at least one);
+    whatever it returns fits the budget when a timed step fits at all."""
+    spent, budget, extra = 30.0 + t_step, 1700.0, 35.0
+    w, k = bench.plan_steps(5, 20, t_step, spent, budget, extra)
+    assert (w, k) == expect
+    assert w >= 3 and k >= 1
+    if t_step * 3 <= budget - spent - extra:
+        assert spent + (w - 1 + k) * t_step + extra <= budget
