@@ -86,3 +86,54 @@ def test_preprocess_nothing_to_deflate_is_algorithm1():
     ref = hh.househt(A, B, nb=4)[:4]
     for a, b in zip(ref, (H, T, Q, Z)):
         assert np.array_equal(a, b)
+
+
+FRONT_MUTATIONS = [
+    # the front end's Q_B applied from the wrong side (Sec. 1)
+    ("H, T, Qh, Z, _ = househt(Qb.T @ A, R, nb=nb)", "H, T, Qh, Z, _ = househt(Qb @ A, R, nb=nb)"),
+    # Q_B left out of the accumulated Q
+    ("return H, T, Qb @ Qh, Z", "return H, T, Qh, Z"),
+    # zero columns moved to the back instead of the front (Sec. 3.4.1)
+    ("perm = zc + [c for c in range(n) if c not in set(zc)]", "perm = [c for c in range(n) if c not in set(zc)] + zc"),
+    # the first l rows of A miss Z22
+    ("H[:l, l:] = A1[:l, l:] @ Z22", "H[:l, l:] = A1[:l, l:]"),
+    # Z22 transposed on the first l rows of B
+    ("T[:l, l:] = B1[:l, l:] @ Z22", "T[:l, l:] = B1[:l, l:] @ Z22.T"),
+    # Q22 transposed in the accumulated Q
+    ("Q[:, l:] = Q[:, l:] @ Q22", "Q[:, l:] = Q[:, l:] @ Q22.T"),
+    # Q_1 applied to B from the wrong side
+    ("B1 = Q1.T @ B0", "B1 = Q1 @ B0"),
+]
+
+
+def _front_mutant(old, new):
+    import os
+    import types
+    src = open(os.path.join(os.path.dirname(front.__file__), "front.py")).read()
+    assert src.count(old) == 1, old
+    mod = types.ModuleType("oracle._front_mutant")
+    mod.__dict__["__package__"] = "oracle"
+    mod.__dict__["__name__"] = "oracle._front_mutant"
+    exec(compile(src.replace(old, new), "front_mutant.py", "exec"), mod.__dict__)
+    return mod
+
+
+@pytest.mark.parametrize("idx", range(len(FRONT_MUTATIONS)))
+def test_planted_front_mistake_is_caught(idx):
+    mod = _front_mutant(*FRONT_MUTATIONS[idx])
+    rng = np.random.default_rng(91)
+    n = 14
+    A, B = rng.standard_normal((n, n)), rng.standard_normal((n, n))
+    A2, B2 = _triu_with_zero_columns(12, [2, 5, 6, 11], 8)
+    caught = False
+    try:
+        H, T, Q, Z = mod.general(A, B, nb=4)
+        r = report(A, B, H, T, Q, Z)
+        assert r["sh"] == 0 and r["st"] == 0 and max(r["oq"], r["oz"], r["ba"], r["bb"]) <= r["tol"], r
+        H, T, Q, Z, l = mod.preprocess(A2, B2, nb=4)
+        r = report(A2, B2, H, T, Q, Z)
+        assert r["sh"] == 0 and r["st"] == 0 and max(r["oq"], r["oz"], r["ba"], r["bb"]) <= r["tol"], r
+        assert not np.any(T[:, :l]) and not np.any(np.tril(H[:, :l], -1))
+    except (AssertionError, ValueError, np.linalg.LinAlgError):
+        caught = True
+    assert caught, FRONT_MUTATIONS[idx][1]
