@@ -81,7 +81,8 @@ typedef struct ht_options {
                           1e-12 (the stated accuracy of the emulated path), redo the reduction with
                           HT_PREC_FP64 from a saved copy of A and B (ht_stats.emu_fallback = 1); allocates
                           2 n^2 + 32 n doubles.  2 = the same with the check treated as failed (a test of the
-                          fallback).  0: off */
+                          fallback).  0: off.  Not applied together with preprocess, nor by
+                          ht_reduce_general (their reductions start from a transformed pencil) */
   int reserved[4];
 } ht_options;
 
