@@ -78,9 +78,13 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=1024)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--config", default="single", choices=["single", "batch"],
-                   help="single: the headline pencil; batch: 512 pencils n ~ U{64..1024} in one "
-                        "ht_reduce_batched call against a loop of ht_reduce calls (not the headline)")
+    p.add_argument("--config", default="single", choices=["single", "batch", "nb-sweep", "graded", "saddle"],
+                   help="single: the headline pencil; the others print one JSON line per measurement and are "
+                        "not the headline: batch: 512 pencils n ~ U{64..1024} in one ht_reduce_batched call "
+                        "against a loop of ht_reduce calls; nb-sweep: the n = 4096 near-infinite pencil in FP64 "
+                        "at panel widths 16, 32, 64; graded: the graded n = 8192 pencil, emulated and FP64; "
+                        "saddle: saddle-point pencils (n = 1000, 4000) without and with the zero-column "
+                        "preprocessing")
     p.add_argument("--batch-count", type=int, default=512)
     p.add_argument("--budget", type=float, default=1700.0,
                    help="wall-clock seconds the whole run must fit; fewer warm-up, then timed, steps if needed")
@@ -497,10 +501,60 @@ def run_batch(args):
         "dtype": "f64", "data": "synthetic", "n_gpus": 1}), flush=True)
 
 
+def run_configs(args):
+    """The other configurations, one JSON line per run (best of two calls;
+    backward errors and orthogonality by 16 Gaussian probes on the GPU)."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_1710_08538_gb300 as ht
+    from paper_1710_08538_gb300 import check, pencils
+
+    def run(kind, n, prec, nb, seed, **kw):
+        A_np, B_np = pencils.make(kind, n, seed)
+        B_np = np.triu(B_np)
+        A0, B0 = ht.colmajor(A_np), ht.colmajor(B_np)
+        del A_np, B_np
+        best, st = None, None
+        for _ in range(2):
+            A, B = A0.clone(), B0.clone()
+            Q, Z = torch.empty_like(A0), torch.empty_like(A0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = ht.reduce(A, B, Q, Z, True, ht.options(nb=nb, precision=prec, **kw), with_stats=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        rep = check.invariants(A0, B0, A, B, Q, Z, probes=16, seed=7)
+        print(json.dumps({"config": args.config, "workload": kind, "n": n,
+                          "precision": "emu" if prec == ht.HT_PREC_EMU else "fp64", "nb": nb, "options": kw,
+                          "s": best, "eff_tflops": f_nom(n) / best / 1e12, "panels": st["panels"],
+                          "early_absorptions": st["early_absorptions"], "ir_steps": st["ir_steps"],
+                          "cols_with_ir": st["cols_with_ir"], "perturbed_pivots": st["perturbed_pivots"],
+                          "bwd_a": rep["bwd_a"], "bwd_b": rep["bwd_b"], "orth_q": rep["orth_q"],
+                          "orth_z": rep["orth_z"],
+                          "structure_ok": rep["h_nonzeros_below_subdiag"] == 0 and rep["t_nonzeros_below_diag"] == 0}),
+              flush=True)
+
+    if args.config == "nb-sweep":
+        for nb in (16, 32, 64):
+            run("near_infinite", 4096, ht.HT_PREC_FP64, nb, 4096)
+    elif args.config == "graded":
+        run("graded", 8192, ht.HT_PREC_EMU, 32, 8192)
+        run("graded", 8192, ht.HT_PREC_FP64, 32, 8192)
+    elif args.config == "saddle":
+        for n in (1000, 4000):
+            for pre in (0, 1):
+                run("saddle_point", n, ht.HT_PREC_FP64, 32, 77, preprocess=pre)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.config == "batch" and a.impl == "ours":
         run_batch(a)
+    elif a.config in ("nb-sweep", "graded", "saddle") and a.impl == "ours":
+        run_configs(a)
     elif a.impl == "reference":
         run_reference(a)
     else:
